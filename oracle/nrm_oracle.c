@@ -1,0 +1,855 @@
+/*
+ * nrm_oracle.c -- plain, slow, serial C oracle for xNRMF / xNRMP
+ * (Novakovic, "Recursive vectorized computation of the vector p-norm",
+ * arXiv 2509.06220).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg do.  It shares no code with the CUDA library: every formula
+ * below is written out again here from the paper.
+ *
+ * Build: C11, -O2 -ffp-contract=off, no fast-math, no FTZ.  With contraction
+ * off every C arithmetic operator below is one IEEE-754 binary64/binary32
+ * operation rounded to nearest-even, and fma() is the only fused operation,
+ * which is what Section 1 assumes ("rounding to nearest") and what the
+ * one-statement-one-instruction reading of Listing 2 requires.
+ *
+ * What is here (each function cites the passage it follows):
+ *   or_k1_d / or_k1_s      v1_hypot, Listing 2 (Section 2)
+ *   or_lp_d / or_lp_s      v1_lp, Listing 5 (Section 4, Eqs. sp and qp)
+ *   sumabs / maxabs        Eqs. vp1 and vpI (Section 4)
+ *   or_pow_d / or_pow_s    the pow[f] that v1_lp needs (Section 4 leaves the
+ *                          choice open); written here from the textbook
+ *                          identities x^y = 2^(y log2 x), ln f = 2 atanh(s),
+ *                          s = (f-1)/(f+1), and the Taylor series of atanh
+ *                          and exp, with double-word (Dekker) arithmetic.
+ *   or_R_*                 R_x, Listing 1 / Eq. r (Section 2)
+ *   or_Z_*                 Z_x generalised to p lanes, Listing 4 (Section 3)
+ *   or_nrm_*               xNRMF / xNRMP = Z then a final R over the lanes
+ *                          (Section 3, recommendation for xNRMF)
+ *   or_nrm_slot_*          the same tree evaluated in "slot form" (a perfect
+ *                          tree whose empty slots are skipped); a second,
+ *                          independent evaluation used to pin or_nrm_*
+ *   or_ref_q128            binary128 reference norm (stands in for the
+ *                          2048-bit MPFR reference of Section 2, Eq. relerr)
+ *   or_ub_relerr           closed-form upper bound of Eq. ubr / Table 3
+ *
+ * Parity status: every function here is pinned by the tests under tests/
+ * (see test_oracle_pins.py); none is "parity unpinned".
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#if defined(__aarch64__)
+typedef long double q128; /* IEEE binary128 on AArch64 Linux */
+#define Q_SQRT sqrtl
+#define Q_POW powl
+#define Q_FABS fabsl
+#elif defined(__x86_64__)
+#include <quadmath.h>
+typedef __float128 q128;
+#define Q_SQRT sqrtq
+#define Q_POW powq
+#define Q_FABS fabsq
+#else
+#error "binary128 reference needs AArch64 long double or x86-64 __float128"
+#endif
+
+#define OR_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------ */
+/* combine operations                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Combine op selector: which per-node operation the tree applies. */
+enum { OP_HYPOT = 0, OP_LP = 1, OP_SUMABS = 2, OP_MAXABS = 3 };
+
+/* v1_hypot (Listing 2, Section 2): every statement is one IEEE operation.
+ * fmin/fmax return the other operand when one is a NaN, so Q is never a NaN
+ * (this also makes K(a,0)=a and K(0,0)=0 exact). */
+OR_API double or_k1_d(double x, double y)
+{
+    const double X = fabs(x);
+    const double Y = fabs(y);
+    const double m = fmin(X, Y);
+    const double M = fmax(X, Y);
+    const double q = m / M;
+    const double Q = fmax(q, 0.0);
+    const double S = fma(Q, Q, 1.0);
+    const double s = sqrt(S);
+    return M * s;
+}
+
+/* v1_hypotf: the single-precision form of Listing 2 (Section 2 says the
+ * S routines substitute float, fabsf and the f-suffixed functions). */
+OR_API float or_k1_s(float x, float y)
+{
+    const float X = fabsf(x);
+    const float Y = fabsf(y);
+    const float m = fminf(X, Y);
+    const float M = fmaxf(X, Y);
+    const float q = m / M;
+    const float Q = fmaxf(q, 0.0f);
+    const float S = fmaf(Q, Q, 1.0f);
+    const float s = sqrtf(S);
+    return M * s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* pow for v1_lp                                                             */
+/* ------------------------------------------------------------------------ */
+
+static inline uint64_t bits_d(double x) { uint64_t u; memcpy(&u, &x, 8); return u; }
+static inline double from_bits_d(uint64_t u) { double x; memcpy(&x, &u, 8); return x; }
+static inline uint32_t bits_s(float x) { uint32_t u; memcpy(&u, &x, 4); return u; }
+static inline float from_bits_s(uint32_t u) { float x; memcpy(&x, &u, 4); return x; }
+
+/* 2^k as a double for -1074 <= k <= 1023, built from its bit pattern. */
+static double pow2_d(int k)
+{
+    if (k >= -1022) return from_bits_d((uint64_t)(k + 1023) << 52);
+    return from_bits_d(1ull << (k + 1074));
+}
+
+static float pow2_s(int k)
+{
+    if (k >= -126) return from_bits_s((uint32_t)(k + 127) << 23);
+    return from_bits_s(1u << (k + 149));
+}
+
+/* ln 2 and 1/ln 2 as double-word constants (hi = RN(c), lo = RN(c - hi)). */
+#define LN2_HI 0x1.62e42fefa39efp-1
+#define LN2_LO 0x1.abc9e3b39803fp-56
+#define ILN2_HI 0x1.71547652b82fep+0
+#define ILN2_LO 0x1.777d0ffda0d24p-56
+#define SQRT2_D 0x1.6a09e667f3bcdp+0
+#define LN2F_HI 0x1.62e430p-1f
+#define LN2F_LO -0x1.05c610p-29f
+#define ILN2F_HI 0x1.715476p+0f
+#define ILN2F_LO 0x1.4ae0c0p-26f
+#define SQRT2_S 0x1.6a09e6p+0f
+
+/*
+ * or_pow_d(x, y) ~ x^y for x >= 0 and finite y > 0: the pow of Listing 5.
+ * The paper leaves the pow to the platform (cr_pow, __builtin_pow, SLEEF);
+ * this one is defined here so that the oracle and the GPU compute the same
+ * bits.  Steps:
+ *  1. x = 2^e f with f in [sqrt(1/2), sqrt(2)).
+ *  2. s = (f-1)/(f+1) as a double-word s_hi + s_lo (f-1 and the rounding
+ *     error of f+1 are exact; the quotient is corrected by its exact FMA
+ *     remainder).
+ *  3. ln f = 2 atanh(s) = 2s + 2s z T(z), z = s^2, T(z) = sum_{j>=0}
+ *     z^j/(2j+3) truncated after 12 terms (|s| <= 0.1716, so the next term
+ *     is below 2^-62 relative).
+ *  4. log2 x = e + ln f / ln 2 and t = y log2 x, both double-word.
+ *  5. t = k + r with k = rint(t), |r| <= 1/2; 2^r = exp(r ln 2) by its
+ *     Taylor series to degree 14 (|r ln 2| <= 0.347), and 2^t = 2^k 2^r.
+ * Exact cases: pow(0,y) = 0, pow(1,y) = 1, pow(inf,y) = inf.
+ */
+OR_API double or_pow_d(double x, double y)
+{
+    if (isnan(x) || isnan(y)) return x + y;
+    if (x == 0.0) return 0.0;
+    if (x == 1.0) return 1.0;
+    if (isinf(x)) return x;
+    /* step 1 */
+    uint64_t b = bits_d(x);
+    int e = 0;
+    if ((b >> 52) == 0) { /* subnormal: scale by 2^54 (exact) */
+        x = x * 0x1p54;
+        b = bits_d(x);
+        e = -54;
+    }
+    e += (int)(b >> 52) - 1023;
+    double f = from_bits_d((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull);
+    if (f > SQRT2_D) { f = f * 0.5; e = e + 1; }
+    /* step 2 */
+    const double a = f - 1.0;
+    const double d_hi = f + 1.0;
+    const double d_lo = f - (d_hi - 1.0);
+    const double s_hi = a / d_hi;
+    double rr = fma(-s_hi, d_hi, a);
+    rr = fma(-s_hi, d_lo, rr);
+    const double s_lo = rr / d_hi;
+    /* step 3 */
+    const double z = s_hi * s_hi;
+    double T = 1.0 / 25.0;
+    T = fma(T, z, 1.0 / 23.0);
+    T = fma(T, z, 1.0 / 21.0);
+    T = fma(T, z, 1.0 / 19.0);
+    T = fma(T, z, 1.0 / 17.0);
+    T = fma(T, z, 1.0 / 15.0);
+    T = fma(T, z, 1.0 / 13.0);
+    T = fma(T, z, 1.0 / 11.0);
+    T = fma(T, z, 1.0 / 9.0);
+    T = fma(T, z, 1.0 / 7.0);
+    T = fma(T, z, 1.0 / 5.0);
+    T = fma(T, z, 1.0 / 3.0);
+    const double c = (2.0 * s_hi) * (z * T);
+    const double L_hi = 2.0 * s_hi;
+    const double L_lo = fma(2.0, s_lo, c);
+    /* step 4: lg = (L_hi + L_lo) / ln 2 */
+    const double g_hi = L_hi * ILN2_HI;
+    double g_lo = fma(L_hi, ILN2_HI, -g_hi);
+    g_lo = fma(L_hi, ILN2_LO, g_lo);
+    g_lo = fma(L_lo, ILN2_HI, g_lo);
+    /* add the exponent: (h, l) = e + g_hi exactly, then l += g_lo */
+    const double ed = (double)e;
+    const double h = ed + g_hi;
+    double l;
+    if (fabs(ed) >= fabs(g_hi)) l = (ed - h) + g_hi;
+    else l = (g_hi - h) + ed;
+    l = l + g_lo;
+    /* t = y (h + l) */
+    const double t_hi = y * h;
+    double t_lo = fma(y, h, -t_hi);
+    t_lo = fma(y, l, t_lo);
+    if (t_hi < -1100.0) return 0.0;
+    if (t_hi > 1100.0) return INFINITY;
+    /* step 5 */
+    const double k = rint(t_hi);
+    const double r0 = t_hi - k; /* exact */
+    const double r_hi = r0 + t_lo;
+    const double r_lo = t_lo - (r_hi - r0);
+    const double u_hi = r_hi * LN2_HI;
+    double u_lo = fma(r_hi, LN2_HI, -u_hi);
+    u_lo = fma(r_hi, LN2_LO, u_lo);
+    u_lo = fma(r_lo, LN2_HI, u_lo);
+    /* E = exp(u) - 1 - u, degree 2..14 in u_hi */
+    double P = 1.0 / 87178291200.0;   /* 1/14! */
+    P = fma(P, u_hi, 1.0 / 6227020800.0); /* 1/13! */
+    P = fma(P, u_hi, 1.0 / 479001600.0);  /* 1/12! */
+    P = fma(P, u_hi, 1.0 / 39916800.0);   /* 1/11! */
+    P = fma(P, u_hi, 1.0 / 3628800.0);    /* 1/10! */
+    P = fma(P, u_hi, 1.0 / 362880.0);     /* 1/9! */
+    P = fma(P, u_hi, 1.0 / 40320.0);      /* 1/8! */
+    P = fma(P, u_hi, 1.0 / 5040.0);       /* 1/7! */
+    P = fma(P, u_hi, 1.0 / 720.0);        /* 1/6! */
+    P = fma(P, u_hi, 1.0 / 120.0);        /* 1/5! */
+    P = fma(P, u_hi, 1.0 / 24.0);         /* 1/4! */
+    P = fma(P, u_hi, 1.0 / 6.0);          /* 1/3! */
+    P = fma(P, u_hi, 0.5);                /* 1/2! */
+    const double E = (u_hi * u_hi) * P;
+    /* m = 1 + u_hi + (u_lo + E) */
+    const double m_hi = 1.0 + u_hi;
+    const double m_err = (1.0 - m_hi) + u_hi; /* exact: |u_hi| < 1 */
+    const double m = m_hi + (m_err + (u_lo + E));
+    const int ki = (int)k;
+    if (ki > 1023) return INFINITY;
+    if (ki < -1074) return 0.0;
+    return m * pow2_d(ki);
+}
+
+/*
+ * or_pow_s(x, y) ~ x^y in binary32, the powf of Listing 5 for S; the same
+ * five steps as or_pow_d with binary32 double-word arithmetic: atanh series
+ * to z^5/13 and the exp series to degree 9.
+ */
+OR_API float or_pow_s(float x, float y)
+{
+    if (isnan(x) || isnan(y)) return x + y;
+    if (x == 0.0f) return 0.0f;
+    if (x == 1.0f) return 1.0f;
+    if (isinf(x)) return x;
+    uint32_t b = bits_s(x);
+    int e = 0;
+    if ((b >> 23) == 0) {
+        x = x * 0x1p25f;
+        b = bits_s(x);
+        e = -25;
+    }
+    e += (int)(b >> 23) - 127;
+    float f = from_bits_s((b & 0x007fffffu) | 0x3f800000u);
+    if (f > SQRT2_S) { f = f * 0.5f; e = e + 1; }
+    const float a = f - 1.0f;
+    const float d_hi = f + 1.0f;
+    const float d_lo = f - (d_hi - 1.0f);
+    const float s_hi = a / d_hi;
+    float rr = fmaf(-s_hi, d_hi, a);
+    rr = fmaf(-s_hi, d_lo, rr);
+    const float s_lo = rr / d_hi;
+    const float z = s_hi * s_hi;
+    float T = 1.0f / 13.0f;
+    T = fmaf(T, z, 1.0f / 11.0f);
+    T = fmaf(T, z, 1.0f / 9.0f);
+    T = fmaf(T, z, 1.0f / 7.0f);
+    T = fmaf(T, z, 1.0f / 5.0f);
+    T = fmaf(T, z, 1.0f / 3.0f);
+    const float c = (2.0f * s_hi) * (z * T);
+    const float L_hi = 2.0f * s_hi;
+    const float L_lo = fmaf(2.0f, s_lo, c);
+    const float g_hi = L_hi * ILN2F_HI;
+    float g_lo = fmaf(L_hi, ILN2F_HI, -g_hi);
+    g_lo = fmaf(L_hi, ILN2F_LO, g_lo);
+    g_lo = fmaf(L_lo, ILN2F_HI, g_lo);
+    const float ed = (float)e;
+    const float h = ed + g_hi;
+    float l;
+    if (fabsf(ed) >= fabsf(g_hi)) l = (ed - h) + g_hi;
+    else l = (g_hi - h) + ed;
+    l = l + g_lo;
+    const float t_hi = y * h;
+    float t_lo = fmaf(y, h, -t_hi);
+    t_lo = fmaf(y, l, t_lo);
+    if (t_hi < -200.0f) return 0.0f;
+    if (t_hi > 200.0f) return INFINITY;
+    const float k = rintf(t_hi);
+    const float r0 = t_hi - k;
+    const float r_hi = r0 + t_lo;
+    const float r_lo = t_lo - (r_hi - r0);
+    const float u_hi = r_hi * LN2F_HI;
+    float u_lo = fmaf(r_hi, LN2F_HI, -u_hi);
+    u_lo = fmaf(r_hi, LN2F_LO, u_lo);
+    u_lo = fmaf(r_lo, LN2F_HI, u_lo);
+    float P = 1.0f / 362880.0f;         /* 1/9! */
+    P = fmaf(P, u_hi, 1.0f / 40320.0f); /* 1/8! */
+    P = fmaf(P, u_hi, 1.0f / 5040.0f);  /* 1/7! */
+    P = fmaf(P, u_hi, 1.0f / 720.0f);   /* 1/6! */
+    P = fmaf(P, u_hi, 1.0f / 120.0f);   /* 1/5! */
+    P = fmaf(P, u_hi, 1.0f / 24.0f);    /* 1/4! */
+    P = fmaf(P, u_hi, 1.0f / 6.0f);     /* 1/3! */
+    P = fmaf(P, u_hi, 0.5f);            /* 1/2! */
+    const float E = (u_hi * u_hi) * P;
+    const float m_hi = 1.0f + u_hi;
+    const float m_err = (1.0f - m_hi) + u_hi;
+    const float m = m_hi + (m_err + (u_lo + E));
+    const int ki = (int)k;
+    if (ki > 127) return INFINITY;
+    if (ki < -149) return 0.0f;
+    return m * pow2_s(ki);
+}
+
+/* v1_lp (Listing 5, Section 4): Eq. sp with the Eq. qp trick of squaring
+ * pow(Q, p/2) inside an fma.  h = p*0.5 and ip = 1.0/p are computed once per
+ * call (Section 4 hoists them to the top of the recursion). */
+OR_API double or_lp_d(double h, double ip, double x, double y)
+{
+    const double X = fabs(x);
+    const double Y = fabs(y);
+    const double m = fmin(X, Y);
+    const double M = fmax(X, Y);
+    const double q = m / M;
+    const double Q = fmax(q, 0.0);
+    const double S = or_pow_d(Q, h);
+    const double Z = fma(S, S, 1.0);
+    const double C = or_pow_d(Z, ip);
+    return M * C;
+}
+
+OR_API float or_lp_s(float h, float ip, float x, float y)
+{
+    const float X = fabsf(x);
+    const float Y = fabsf(y);
+    const float m = fminf(X, Y);
+    const float M = fmaxf(X, Y);
+    const float q = m / M;
+    const float Q = fmaxf(q, 0.0f);
+    const float S = or_pow_s(Q, h);
+    const float Z = fmaf(S, S, 1.0f);
+    const float C = or_pow_s(Z, ip);
+    return M * C;
+}
+
+/* p = 1 (Eq. vp1): |x| + |y|.  p = inf (Eq. vpI): max(|x|, |y|), exact. */
+static double sumabs_d(double x, double y) { return fabs(x) + fabs(y); }
+static float sumabs_s(float x, float y) { return fabsf(x) + fabsf(y); }
+static double maxabs_d(double x, double y) { return fmax(fabs(x), fabs(y)); }
+static float maxabs_s(float x, float y) { return fmaxf(fabsf(x), fabsf(y)); }
+
+typedef struct { int op; double h, ip; } comb_d;
+typedef struct { int op; float h, ip; } comb_s;
+
+static double comb_apply_d(const comb_d *c, double x, double y)
+{
+    switch (c->op) {
+    case OP_HYPOT: return or_k1_d(x, y);
+    case OP_LP: return or_lp_d(c->h, c->ip, x, y);
+    case OP_SUMABS: return sumabs_d(x, y);
+    default: return maxabs_d(x, y);
+    }
+}
+
+static float comb_apply_s(const comb_s *c, float x, float y)
+{
+    switch (c->op) {
+    case OP_HYPOT: return or_k1_s(x, y);
+    case OP_LP: return or_lp_s(c->h, c->ip, x, y);
+    case OP_SUMABS: return sumabs_s(x, y);
+    default: return maxabs_s(x, y);
+    }
+}
+
+/* Choose the combine for a given p (Section 4): p = 2 is xNRMF (v1_hypot),
+ * p = 1 sumabs, p = inf maxabs, any other p > 0 v1_lp with p/2 and 1/p
+ * computed once here. */
+static comb_d comb_for_d(double p)
+{
+    comb_d c = {OP_HYPOT, 0.0, 0.0};
+    if (p == 2.0) c.op = OP_HYPOT;
+    else if (p == 1.0) c.op = OP_SUMABS;
+    else if (isinf(p)) c.op = OP_MAXABS;
+    else { c.op = OP_LP; c.h = p * 0.5; c.ip = 1.0 / p; }
+    return c;
+}
+
+static comb_s comb_for_s(float p)
+{
+    comb_s c = {OP_HYPOT, 0.0f, 0.0f};
+    if (p == 2.0f) c.op = OP_HYPOT;
+    else if (p == 1.0f) c.op = OP_SUMABS;
+    else if (isinf(p)) c.op = OP_MAXABS;
+    else { c.op = OP_LP; c.h = p * 0.5f; c.ip = 1.0f / p; }
+    return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* R_x: the scalar recursion of Listing 1 / Eq. r                           */
+/* ------------------------------------------------------------------------ */
+
+/* R(n, x): n == 1 -> |x0|; n == 2 -> op(x0, x1); otherwise split into a left
+ * part of ceil(n/2) and a right part of floor(n/2), recurse on both, and
+ * combine (Listing 1). */
+static double R_d(int64_t n, const double *x, const comb_d *c)
+{
+    if (n == 1) return fabs(x[0]);
+    if (n == 2) return comb_apply_d(c, x[0], x[1]);
+    const int64_t p = (n >> 1) + (n & 1);
+    const int64_t q = n - p;
+    const double fp = R_d(p, x, c);
+    const double fq = R_d(q, x + p, c);
+    return comb_apply_d(c, fp, fq);
+}
+
+static float R_s(int64_t n, const float *x, const comb_s *c)
+{
+    if (n == 1) return fabsf(x[0]);
+    if (n == 2) return comb_apply_s(c, x[0], x[1]);
+    const int64_t p = (n >> 1) + (n & 1);
+    const int64_t q = n - p;
+    const float fp = R_s(p, x, c);
+    const float fq = R_s(q, x + p, c);
+    return comb_apply_s(c, fp, fq);
+}
+
+/* The scalar algorithm H_x (R with v1_hypot) or its p-norm form.  n == 0
+ * returns +0 (Listing 1 assumes n > 0; +0 is the norm of the empty array). */
+OR_API double or_R_d(int64_t n, const double *x, double p)
+{
+    if (n <= 0) return 0.0;
+    comb_d c = comb_for_d(p);
+    return R_d(n, x, &c);
+}
+
+OR_API float or_R_s(int64_t n, const float *x, float p)
+{
+    if (n <= 0) return 0.0f;
+    comb_s c = comb_for_s(p);
+    return R_s(n, x, &c);
+}
+
+/* Trace of R's operations in completion order (Eq. r): for each operation
+ * record (kind, first, last) with kind 1 = |x| leaf, 2 = hypot of two input
+ * elements (a bold leaf of Eq. r), 3 = hypot of two partial norms; first and
+ * last are the 1-based element range the operation covers. */
+static void R_trace(int64_t n, int64_t off, int64_t *ops, int64_t *k)
+{
+    if (n == 1) { ops[3 * *k] = 1; ops[3 * *k + 1] = off + 1; ops[3 * *k + 2] = off + 1; (*k)++; return; }
+    if (n == 2) { ops[3 * *k] = 2; ops[3 * *k + 1] = off + 1; ops[3 * *k + 2] = off + 2; (*k)++; return; }
+    const int64_t p = (n >> 1) + (n & 1);
+    R_trace(p, off, ops, k);
+    R_trace(n - p, off + p, ops, k);
+    ops[3 * *k] = 3; ops[3 * *k + 1] = off + 1; ops[3 * *k + 2] = off + n; (*k)++;
+}
+
+OR_API int64_t or_R_trace(int64_t n, int64_t *ops)
+{
+    int64_t k = 0;
+    if (n > 0) R_trace(n, 0, ops, &k);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Z_x: the vectorised recursion of Listing 4, generalised to P lanes       */
+/* ------------------------------------------------------------------------ */
+
+/* Z(n, x) -> f[0..P-1] (Listing 4 with 8 replaced by P):
+ *   r = n mod P, m = ceil(n / P) vectors;
+ *   m == 1: f = |x[0..P)|, or |TAIL| with the lanes past n set to zero;
+ *   m == 2: f = op(x[0..P), second vector), the second being |TAIL| via Z
+ *           when r > 0;
+ *   else  : w = ceil(m/2) full vectors on the left, Z on both parts, and f =
+ *           op lane-wise. */
+static void Z_d(int64_t n, const double *x, int P, const comb_d *c, double *f)
+{
+    const int64_t r = n % P;
+    const int64_t m = n / P + (r != 0);
+    if (m == 1) {
+        const int64_t cnt = r ? r : P;
+        for (int l = 0; l < P; ++l) f[l] = (l < cnt) ? fabs(x[l]) : 0.0;
+        return;
+    }
+    double *g = (double *)malloc(sizeof(double) * (size_t)P);
+    if (m == 2) {
+        if (r) Z_d(r, x + P, P, c, g);
+        else for (int l = 0; l < P; ++l) g[l] = x[P + l];
+        for (int l = 0; l < P; ++l) f[l] = comb_apply_d(c, x[l], g[l]);
+        free(g);
+        return;
+    }
+    const int64_t w = (m >> 1) + (m & 1);
+    const int64_t p = w * P;
+    const int64_t q = n - p;
+    Z_d(p, x, P, c, f);
+    Z_d(q, x + p, P, c, g);
+    for (int l = 0; l < P; ++l) f[l] = comb_apply_d(c, f[l], g[l]);
+    free(g);
+}
+
+static void Z_s(int64_t n, const float *x, int P, const comb_s *c, float *f)
+{
+    const int64_t r = n % P;
+    const int64_t m = n / P + (r != 0);
+    if (m == 1) {
+        const int64_t cnt = r ? r : P;
+        for (int l = 0; l < P; ++l) f[l] = (l < cnt) ? fabsf(x[l]) : 0.0f;
+        return;
+    }
+    float *g = (float *)malloc(sizeof(float) * (size_t)P);
+    if (m == 2) {
+        if (r) Z_s(r, x + P, P, c, g);
+        else for (int l = 0; l < P; ++l) g[l] = x[P + l];
+        for (int l = 0; l < P; ++l) f[l] = comb_apply_s(c, x[l], g[l]);
+        free(g);
+        return;
+    }
+    const int64_t w = (m >> 1) + (m & 1);
+    const int64_t p = w * P;
+    const int64_t q = n - p;
+    Z_s(p, x, P, c, f);
+    Z_s(q, x + p, P, c, g);
+    for (int l = 0; l < P; ++l) f[l] = comb_apply_s(c, f[l], g[l]);
+    free(g);
+}
+
+/* The lane partials of Z for the given p (exported for the lane-grouping
+ * pin of the p = 4, n = 16 example of Section 3). */
+OR_API void or_Z_d(int64_t n, const double *x, int P, double p, double *f)
+{
+    comb_d c = comb_for_d(p);
+    if (n <= 0) { for (int l = 0; l < P; ++l) f[l] = 0.0; return; }
+    Z_d(n, x, P, &c, f);
+}
+
+OR_API void or_Z_s(int64_t n, const float *x, int P, float p, float *f)
+{
+    comb_s c = comb_for_s(p);
+    if (n <= 0) { for (int l = 0; l < P; ++l) f[l] = 0.0f; return; }
+    Z_s(n, x, P, &c, f);
+}
+
+/* xNRMF / xNRMP with lane width P: Z, then the final reduction R over the P
+ * lane partials with the same combine (Section 3 recommends Z paired with a
+ * recursive final reduction; here R uses the same op as the tree). */
+OR_API double or_nrm_d(int64_t n, const double *x, int P, double p)
+{
+    if (n <= 0) return 0.0;
+    comb_d c = comb_for_d(p);
+    double *f = (double *)malloc(sizeof(double) * (size_t)P);
+    Z_d(n, x, P, &c, f);
+    const double v = R_d(P, f, &c);
+    free(f);
+    return v;
+}
+
+OR_API float or_nrm_s(int64_t n, const float *x, int P, float p)
+{
+    if (n <= 0) return 0.0f;
+    comb_s c = comb_for_s(p);
+    float *f = (float *)malloc(sizeof(float) * (size_t)P);
+    Z_s(n, x, P, &c, f);
+    const float v = R_s(P, f, &c);
+    free(f);
+    return v;
+}
+
+/* Batched form: out[i] = or_nrm of x[off[i] .. off[i+1]). */
+OR_API void or_nrm_batch_d(int64_t B, const int64_t *off, const double *x, int P, double p, double *out)
+{
+    for (int64_t i = 0; i < B; ++i) out[i] = or_nrm_d(off[i + 1] - off[i], x + off[i], P, p);
+}
+
+OR_API void or_nrm_batch_s(int64_t B, const int64_t *off, const float *x, int P, float p, float *out)
+{
+    for (int64_t i = 0; i < B; ++i) out[i] = or_nrm_s(off[i + 1] - off[i], x + off[i], P, p);
+}
+
+/* ------------------------------------------------------------------------ */
+/* slot form: the same vector-row tree as a perfect tree with empty slots   */
+/* ------------------------------------------------------------------------ */
+
+/* Bit reversal of the low d bits of j. */
+static uint64_t brev_bits(uint64_t j, int d)
+{
+    uint64_t r = 0;
+    for (int i = 0; i < d; ++i) { r = (r << 1) | (j & 1); j >>= 1; }
+    return r;
+}
+
+/*
+ * Second evaluation of Z: the ceil-split tree over the m = ceil(n/P) vector
+ * rows is embedded in a perfect binary tree of depth D = ceil(lg m); leaf
+ * slot j holds a row iff brev_D(j) < m, occupied slots hold the rows in array
+ * order, and a node with one empty child passes the other child through
+ * unchanged (Listing 4 never combines with an empty part).  The combine is
+ * done bottom-up, level by level.  This is the form the GPU evaluates; it
+ * is written independently of Z_d above so that a test can pin one against
+ * the other.
+ */
+OR_API double or_nrm_slot_d(int64_t n, const double *x, int P, double p)
+{
+    if (n <= 0) return 0.0;
+    comb_d c = comb_for_d(p);
+    const int64_t m = (n + P - 1) / P;
+    int D = 0;
+    while ((1ll << D) < m) ++D;
+    const int64_t S = 1ll << D;
+    /* level-D values: S slots x P lanes, plus an occupancy flag */
+    double *v = (double *)malloc(sizeof(double) * (size_t)(S * P));
+    unsigned char *occ = (unsigned char *)malloc((size_t)S);
+    int64_t row = 0;
+    for (int64_t j = 0; j < S; ++j) {
+        occ[j] = brev_bits((uint64_t)j, D) < (uint64_t)m;
+        if (!occ[j]) continue;
+        for (int l = 0; l < P; ++l) {
+            const int64_t i = row * P + l;
+            v[j * P + l] = (i < n) ? fabs(x[i]) : 0.0;
+        }
+        ++row;
+    }
+    for (int64_t w = S; w > 1; w >>= 1) {
+        for (int64_t j = 0; j < w / 2; ++j) {
+            const int64_t a = 2 * j, b = 2 * j + 1;
+            if (occ[a] && occ[b]) {
+                for (int l = 0; l < P; ++l) v[j * P + l] = comb_apply_d(&c, v[a * P + l], v[b * P + l]);
+            } else if (occ[a]) {
+                for (int l = 0; l < P; ++l) v[j * P + l] = v[a * P + l];
+            } else if (occ[b]) {
+                for (int l = 0; l < P; ++l) v[j * P + l] = v[b * P + l];
+            }
+            occ[j] = occ[a] | occ[b];
+        }
+    }
+    /* final reduction: perfect tree over the P lanes (P a power of two), as
+     * R's ceil split gives for such P */
+    for (int w = P; w > 1; w >>= 1)
+        for (int l = 0; l < w / 2; ++l) v[l] = comb_apply_d(&c, v[2 * l], v[2 * l + 1]);
+    const double out = (P == 1) ? fabs(v[0]) : v[0];
+    free(v);
+    free(occ);
+    return out;
+}
+
+OR_API float or_nrm_slot_s(int64_t n, const float *x, int P, float p)
+{
+    if (n <= 0) return 0.0f;
+    comb_s c = comb_for_s(p);
+    const int64_t m = (n + P - 1) / P;
+    int D = 0;
+    while ((1ll << D) < m) ++D;
+    const int64_t S = 1ll << D;
+    float *v = (float *)malloc(sizeof(float) * (size_t)(S * P));
+    unsigned char *occ = (unsigned char *)malloc((size_t)S);
+    int64_t row = 0;
+    for (int64_t j = 0; j < S; ++j) {
+        occ[j] = brev_bits((uint64_t)j, D) < (uint64_t)m;
+        if (!occ[j]) continue;
+        for (int l = 0; l < P; ++l) {
+            const int64_t i = row * P + l;
+            v[j * P + l] = (i < n) ? fabsf(x[i]) : 0.0f;
+        }
+        ++row;
+    }
+    for (int64_t w = S; w > 1; w >>= 1) {
+        for (int64_t j = 0; j < w / 2; ++j) {
+            const int64_t a = 2 * j, b = 2 * j + 1;
+            if (occ[a] && occ[b]) {
+                for (int l = 0; l < P; ++l) v[j * P + l] = comb_apply_s(&c, v[a * P + l], v[b * P + l]);
+            } else if (occ[a]) {
+                for (int l = 0; l < P; ++l) v[j * P + l] = v[a * P + l];
+            } else if (occ[b]) {
+                for (int l = 0; l < P; ++l) v[j * P + l] = v[b * P + l];
+            }
+            occ[j] = occ[a] | occ[b];
+        }
+    }
+    for (int w = P; w > 1; w >>= 1)
+        for (int l = 0; l < w / 2; ++l) v[l] = comb_apply_s(&c, v[2 * l], v[2 * l + 1]);
+    const float out = (P == 1) ? fabsf(v[0]) : v[0];
+    free(v);
+    free(occ);
+    return out;
+}
+
+/* ------------------------------------------------------------------------ */
+/* binary128 reference (stands in for the MPFR reference of Eq. relerr)     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const void *x;
+    int64_t n;
+    int is_double;
+    int kind; /* 0: sum x^2, 1: sum |x|, 2: sum |x|^p, 3: max |x| */
+    q128 p;
+    q128 result;
+} q_job;
+
+/* pairwise sum of the terms of x[0..n) (recursion on halves; the relative
+ * error of such a sum is below lg(n) * 2^-113, far under the tolerances) */
+static q128 q_term(const q_job *jb, int64_t i)
+{
+    q128 v = jb->is_double ? (q128)((const double *)jb->x)[i] : (q128)((const float *)jb->x)[i];
+    v = Q_FABS(v);
+    switch (jb->kind) {
+    case 0: return v * v;
+    case 1: return v;
+    case 2: return (v == 0) ? (q128)0 : Q_POW(v, jb->p);
+    default: return v;
+    }
+}
+
+static q128 q_sum(const q_job *jb, int64_t lo, int64_t n)
+{
+    if (n <= 8) {
+        q128 s = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            q128 t = q_term(jb, lo + i);
+            if (jb->kind == 3) { if (t > s) s = t; }
+            else s += t;
+        }
+        return s;
+    }
+    const int64_t h = n / 2;
+    q128 a = q_sum(jb, lo, h), b = q_sum(jb, lo + h, n - h);
+    if (jb->kind == 3) return a > b ? a : b;
+    return a + b;
+}
+
+static void *q_thread(void *arg)
+{
+    q_job *jb = (q_job *)arg;
+    jb->result = q_sum(jb, 0, jb->n);
+    return NULL;
+}
+
+/* Reference p-norm of x[0..n) in binary128, returned as a double-word
+ * (hi, lo) with hi = RN_double(v) and lo = RN_double(v - hi).  p = 2 sums
+ * exact squares, p = 1 sums |x|, p = inf takes max |x|, other p sum
+ * |x|^p with the binary128 pow.  nthreads contiguous chunks are summed in
+ * parallel and then added in chunk order. */
+OR_API void or_ref_q128(int64_t n, const void *x, int is_double, double p, int nthreads, double *hi, double *lo)
+{
+    int kind;
+    if (p == 2.0) kind = 0;
+    else if (p == 1.0) kind = 1;
+    else if (isinf(p)) kind = 3;
+    else kind = 2;
+    if (nthreads < 1) nthreads = 1;
+    if (n < (int64_t)nthreads * 4096) nthreads = 1;
+    q_job *jobs = (q_job *)calloc((size_t)nthreads, sizeof(q_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    const int64_t chunk = (n + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; ++t) {
+        const int64_t lo_i = (int64_t)t * chunk;
+        int64_t cnt = n - lo_i;
+        if (cnt > chunk) cnt = chunk;
+        if (cnt < 0) cnt = 0;
+        jobs[t].x = is_double ? (const void *)((const double *)x + lo_i) : (const void *)((const float *)x + lo_i);
+        jobs[t].n = cnt;
+        jobs[t].is_double = is_double;
+        jobs[t].kind = kind;
+        jobs[t].p = (q128)p;
+        jobs[t].result = 0;
+    }
+    if (nthreads == 1) q_thread(&jobs[0]);
+    else {
+        for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, q_thread, &jobs[t]);
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    }
+    q128 s = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (kind == 3) { if (jobs[t].result > s) s = jobs[t].result; }
+        else s += jobs[t].result;
+    }
+    q128 v;
+    if (kind == 0) v = Q_SQRT(s);
+    else if (kind == 1 || kind == 3) v = s;
+    else v = (s == 0) ? (q128)0 : Q_POW(s, (q128)1 / (q128)p);
+    const double h = (double)v;
+    *hi = h;
+    *lo = (double)(v - (q128)h);
+    free(jobs);
+    free(th);
+}
+
+/* ------------------------------------------------------------------------ */
+/* error bounds                                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Closed form of the upper bound ub relerr (Eq. ubr) for a recursion whose
+ * longest leaf-to-root path has `depth` hypot operations, each with relative
+ * error factor at most 1 + eps' (Theorem 3 with equal bounds in both
+ * subtrees): ub = ((1 + eps')^depth - 1) / eps.  which = 0: A (cr_hypot,
+ * eps' = eps); which = 1: H (v1_hypot, 1 + eps' from Eq. reH).  prec = 0:
+ * eps = 2^-53 (D); prec = 1: eps = 2^-24 (S).  Evaluated in binary128 and
+ * returned as (hi, lo).  Table 3 prints this value for n = 2^k, depth = k.
+ */
+OR_API void or_ub_relerr(int depth, int prec, int which, double *hi, double *lo)
+{
+    const q128 eps = prec ? (q128)0x1p-24 : (q128)0x1p-53;
+    q128 f;
+    if (which == 0) f = 1 + eps;
+    else {
+        const q128 a = 1 + eps;
+        const q128 a52 = a * a * Q_SQRT(a); /* (1+eps)^(5/2) */
+        f = a52 * Q_SQRT(1 + eps * (2 + eps) / 2);
+    }
+    q128 pw = 1;
+    for (int i = 0; i < depth; ++i) pw *= f;
+    const q128 v = (pw - 1) / eps;
+    const double h = (double)v;
+    *hi = h;
+    *lo = (double)(v - (q128)h);
+}
+
+/* Lower factor 1 + eps'^- of Eq. reH, (hi, lo), for the tests. */
+OR_API void or_reH_factors(int prec, double *lo_hi, double *lo_lo, double *up_hi, double *up_lo)
+{
+    const q128 eps = prec ? (q128)0x1p-24 : (q128)0x1p-53;
+    const q128 b = 1 - eps;
+    const q128 lower = b * b * Q_SQRT(b) * Q_SQRT(1 - eps * (2 - eps) / 2);
+    const q128 a = 1 + eps;
+    const q128 upper = a * a * Q_SQRT(a) * Q_SQRT(1 + eps * (2 + eps) / 2);
+    *lo_hi = (double)lower;
+    *lo_lo = (double)(lower - (q128)*lo_hi);
+    *up_hi = (double)upper;
+    *up_lo = (double)(upper - (q128)*up_hi);
+}
+
+/* Tree depth of the GPU tree for n elements and lane width P: number of
+ * combine levels on the longest leaf-to-root path = ceil(lg ceil(n/P)) +
+ * lg P (the row tree, then R over the P lanes). */
+OR_API int or_tree_depth(int64_t n, int P)
+{
+    if (n <= 0) return 0;
+    const int64_t m = (n + P - 1) / P;
+    int D = 0;
+    while ((1ll << D) < m) ++D;
+    int L = 0;
+    while ((1 << L) < P) ++L;
+    return D + L;
+}

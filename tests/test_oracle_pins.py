@@ -1,0 +1,505 @@
+"""Pins for the C oracle: it is checked against what the paper and the
+mathematics fix, never against itself or the CUDA path.
+
+Each test names the passage it pins.  Together they are chosen so that a
+plausible slip in the oracle (a dropped term, a wrong sign, a transposed
+operand, a wrong split or pairing) fails at least one of them.
+"""
+import math
+import random
+import struct
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_06220_gb300 import inputs
+from conftest import golden_rows
+
+EPS_D = 2.0 ** -53
+EPS_S = 2.0 ** -24
+mpmath.mp.prec = 2300  # exact for sums of squares of any binary64 values
+
+
+def exact_pnorm(xs, p):
+    """Exact-to-2300-bits p-norm of a short list (brute force)."""
+    if p == 2:
+        s = mpmath.mpf(0)
+        for v in xs:
+            s += mpmath.mpf(float(v)) ** 2
+        return mpmath.sqrt(s)
+    if p == 1:
+        return sum((abs(mpmath.mpf(float(v))) for v in xs), mpmath.mpf(0))
+    if p == math.inf:
+        return max(abs(mpmath.mpf(float(v))) for v in xs)
+    pp = mpmath.mpf(p)
+    s = sum((abs(mpmath.mpf(float(v))) ** pp for v in xs), mpmath.mpf(0))
+    return s ** (1 / pp)
+
+
+def rel(value, exact):
+    if exact == 0:
+        return 0.0 if value == 0 else math.inf
+    return float(abs(mpmath.mpf(float(value)) - exact) / exact)
+
+
+def ub(depth, prec="D", which="H"):
+    hi, lo = oracle.ub_relerr(depth, prec, which)
+    return hi + lo
+
+
+def rng_d(seed, n, emin=-20, emax=20):
+    return inputs.vector(n, seed=seed, vec=7, dtype=np.float64, emin=emin, emax=emax)
+
+
+def rng_s(seed, n, emin=-20, emax=20):
+    return inputs.vector(n, seed=seed, vec=7, dtype=np.float32, emin=emin, emax=emax)
+
+
+def same_bits(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return a.dtype == b.dtype and a.tobytes() == b.tobytes()
+
+
+# ---------------------------------------------------------------------------
+# v1_hypot (Listing 2) and Eq. reH
+# ---------------------------------------------------------------------------
+
+def test_k1_special_values():
+    """Listing 2: K(a,0) = a, K(0,0) = 0 (Q = fmax(NaN,0) = 0), symmetry, the
+    Pythagorean triple 3-4-5 (every step exact), infinities."""
+    for dt in (np.float64, np.float32):
+        assert oracle.k1(3.0, 4.0, dt) == 5.0
+        assert oracle.k1(-4.0, 3.0, dt) == 5.0
+        assert oracle.k1(0.0, 0.0, dt) == 0.0
+        assert not math.copysign(1.0, float(oracle.k1(-0.0, 0.0, dt))) < 0
+        assert math.isinf(oracle.k1(math.inf, 1.0, dt))
+        assert math.isinf(oracle.k1(math.inf, math.inf, dt))
+        assert math.isinf(oracle.k1(-math.inf, 0.0, dt))
+    r = random.Random(1)
+    for _ in range(2000):
+        a = r.uniform(-1e3, 1e3) * 2.0 ** r.randint(-60, 60)
+        b = r.uniform(-1e3, 1e3) * 2.0 ** r.randint(-60, 60)
+        assert oracle.k1(a, 0.0) == abs(a)
+        assert oracle.k1(0.0, a) == abs(a)
+        assert same_bits(oracle.k1(a, b), oracle.k1(b, a))
+        assert same_bits(oracle.k1(a, b), oracle.k1(-a, b))
+        fa = np.float32(a)
+        assert oracle.k1(fa, 0.0, np.float32) == abs(fa)
+
+
+def test_k1_nan_reading():
+    """Listing 2's closing comment: fmin/fmax return the other argument when
+    one is a NaN, so K(NaN, y) = |y| sqrt(2)'s rounding and K(NaN, 0) = 0."""
+    s2 = math.sqrt(2.0)
+    assert oracle.k1(math.nan, 1.0) == s2
+    assert oracle.k1(math.nan, 0.0) == 0.0
+    assert math.isnan(oracle.k1(math.nan, math.nan))
+
+
+@pytest.mark.parametrize("dt,eps", [(np.float64, EPS_D), (np.float32, EPS_S)])
+def test_k1_within_reH(dt, eps):
+    """Eq. reH: the relative error factor of v1_hypot lies strictly between
+    (1-eps)^(5/2) sqrt(1 - eps(2-eps)/2) and (1+eps)^(5/2) sqrt(1 + eps(2+eps)/2)."""
+    (lo_h, lo_l), (up_h, up_l) = oracle.reH_factors("D" if dt == np.float64 else "S")
+    lower = mpmath.mpf(lo_h) + mpmath.mpf(lo_l)
+    upper = mpmath.mpf(up_h) + mpmath.mpf(up_l)
+    assert float((upper - 1) / eps) == pytest.approx(3.0, rel=1e-6)
+    r = random.Random(2)
+    worst = 0.0
+    for _ in range(4000):
+        a = dt(r.uniform(0.5, 2.0) * 2.0 ** r.randint(-30, 30))
+        b = dt(r.uniform(0.5, 2.0) * 2.0 ** r.randint(-30, 30))
+        h = oracle.k1(a, b, dt)
+        ex = mpmath.sqrt(mpmath.mpf(float(a)) ** 2 + mpmath.mpf(float(b)) ** 2)
+        f = mpmath.mpf(float(h)) / ex
+        assert lower < f < upper
+        worst = max(worst, abs(float(f - 1)) / eps)
+    assert worst > 0.5  # the check is not vacuous
+
+
+def test_reH_factors_closed_form():
+    """Eq. reH evaluated by the oracle equals the formula evaluated here."""
+    for prec, eps in (("D", mpmath.mpf(2) ** -53), ("S", mpmath.mpf(2) ** -24)):
+        (lo_h, lo_l), (up_h, up_l) = oracle.reH_factors(prec)
+        up = (1 + eps) ** mpmath.mpf(2.5) * mpmath.sqrt(1 + eps * (2 + eps) / 2)
+        lo = (1 - eps) ** mpmath.mpf(2.5) * mpmath.sqrt(1 - eps * (2 - eps) / 2)
+        assert abs(mpmath.mpf(up_h) + up_l - up) < mpmath.mpf(2) ** -100
+        assert abs(mpmath.mpf(lo_h) + lo_l - lo) < mpmath.mpf(2) ** -100
+
+
+# ---------------------------------------------------------------------------
+# Table 3 / Eq. ubr
+# ---------------------------------------------------------------------------
+
+def test_table3_bounds():
+    """The bound evaluator reproduces the A and H columns of Table 3 for
+    n = 2^k, k = 1..30 (depth k), to the 18 printed digits."""
+    rows = golden_rows("table3_ub_relerr.txt")
+    assert len(rows) == 30
+    for k, a_s, h_s in rows:
+        k = int(k)
+        for which, printed in (("A", a_s), ("H", h_s)):
+            hi, lo = oracle.ub_relerr(k, "D", which)
+            v = mpmath.mpf(hi) + mpmath.mpf(lo)
+            # printed with 18 significant digits: compare to half a unit there
+            p = mpmath.mpf(printed)
+            assert abs(v - p) <= mpmath.mpf(10) ** (mpmath.floor(mpmath.log10(p)) - 17) * 0.51, (k, which)
+
+
+# ---------------------------------------------------------------------------
+# Tree shape: Eq. r, the Y_D(16,x) example, P = 1, slot form
+# ---------------------------------------------------------------------------
+
+def test_eq_r_order_n7():
+    """Eq. r: completion order of R_x on 7 elements."""
+    kinds = {"leaf1": 1, "leaf2": 2, "node": 3}
+    expect = [(kinds[k], int(a), int(b)) for _, k, a, b in golden_rows("eq_r_order_n7.txt")]
+    assert oracle.R_trace(7) == expect
+
+
+def test_R_split_rule():
+    """Listing 1: left part ceil(n/2) >= right part; R on n = 3 is
+    K(K(x1,x2), |x3|) and n = 5 is K(K(K(x1,x2),|x3|), K(x4,x5))."""
+    x = rng_d(3, 5)
+    k = oracle.k1
+    assert oracle.R(x[:3]) == k(k(x[0], x[1]), abs(x[2]))
+    assert oracle.R(x) == k(k(k(x[0], x[1]), abs(x[2])), k(x[3], x[4]))
+    assert oracle.R(x[:1]) == abs(x[0])
+
+
+def test_yd16_lane_grouping():
+    """Section 3, Y_D(16, x) with 4 lanes: lane l pairs (x_l, x_{l+4}) and
+    (x_{l+8}, x_{l+12})."""
+    x = rng_d(4, 16)
+    f = oracle.Z(x, 4)
+    k = oracle.k1
+    for lane, a, b in golden_rows("yd16_lanes.txt"):
+        l = int(lane) - 1
+        i, j = (int(t) - 1 for t in a.split(","))
+        u, v = (int(t) - 1 for t in b.split(","))
+        assert f[l] == k(k(x[i], x[j]), k(x[u], x[v]))
+
+
+def test_head_tail_example_n13_p8():
+    """Section 3's n = 13, p = 8 picture: one full vector then a TAIL of 5
+    elements padded with zero lanes; lanes >= 5 keep |x_l| alone."""
+    x = rng_d(5, 13)
+    f = oracle.Z(x, 8)
+    k = oracle.k1
+    for l in range(8):
+        if l < 5:
+            assert f[l] == k(x[l], x[8 + l])
+        else:
+            assert f[l] == k(x[l], 0.0) == abs(x[l])
+
+
+def test_p1_equals_R():
+    """With one lane, Z is R (the vector recursion reduces to Listing 1)."""
+    for n in (1, 2, 3, 7, 31, 64, 100, 1000):
+        x = rng_d(n, n)
+        assert same_bits(oracle.nrm(x, P=1), oracle.R(x))
+        xs = rng_s(n, n)
+        assert same_bits(oracle.nrm(xs, P=1), oracle.R(xs))
+
+
+def test_scalar_norm_is_abs():
+    """Section 1: the norm of a scalar is |x| (all p, both precisions)."""
+    for v in (1.5, -3.25, 2.0 ** -1074, -(2.0 ** 1023), 0.0):
+        for p in (2.0, 1.0, 3.0, math.inf):
+            assert oracle.nrm(np.array([v])) == abs(v)
+            assert oracle.nrm(np.array([v]), p=p) == abs(v)
+            assert oracle.nrm(np.array([v], np.float32), p=p) == abs(np.float32(v))
+
+
+@pytest.mark.parametrize("P", [4, 8, 64])
+def test_slot_form_equals_Z_double(P):
+    """The slot form (perfect tree, slot j occupied iff brev(j) < m) equals
+    Listing 4's recursion bit for bit, for every n up to 40 rows and random
+    larger n."""
+    ns = list(range(1, 40 * P + 1)) if P < 64 else list(range(1, 4 * P + 1)) + list(range(4 * P, 3000 * 1, 7))
+    r = random.Random(P)
+    ns += [r.randint(1, 200000) for _ in range(10)]
+    base = rng_d(11, max(ns))
+    for n in ns:
+        x = base[:n]
+        for p in (2.0, 1.0):
+            assert same_bits(oracle.nrm(x, p, P), oracle.nrm_slot(x, p, P)), (n, p)
+
+
+@pytest.mark.parametrize("P", [8, 128])
+def test_slot_form_equals_Z_single(P):
+    r = random.Random(P + 1)
+    ns = list(range(1, 3 * P + 2)) + [r.randint(1, 300000) for _ in range(8)]
+    base = rng_s(12, max(ns))
+    for n in ns:
+        x = base[:n]
+        for p in (2.0, 3.0):
+            assert same_bits(oracle.nrm(x, p, P), oracle.nrm_slot(x, p, P)), (n, p)
+
+
+def test_lane_width_changes_bits():
+    """Section 3: the vectorised results are reproducible only for a fixed
+    lane count -- different widths pair the elements differently."""
+    x = rng_d(13, 100000)
+    vals = {float(oracle.nrm(x, P=P)) for P in (1, 8, 16, 64)}
+    assert len(vals) > 1
+
+
+# ---------------------------------------------------------------------------
+# accuracy: brute force, bounds, closed forms
+# ---------------------------------------------------------------------------
+
+def test_brute_force_small_n_within_bound():
+    """Theorem 3 / Eq. ubr: for n <= 16 the relative error against the exact
+    norm is below the bound for the tree's depth (H column closed form)."""
+    r = random.Random(5)
+    for trial in range(300):
+        n = r.randint(1, 16)
+        for dt, eps, prec in ((np.float64, EPS_D, "D"), (np.float32, EPS_S, "S")):
+            x = inputs.vector(n, seed=trial, vec=n, dtype=dt, emin=-30, emax=30)
+            P = oracle.P_D if dt == np.float64 else oracle.P_S
+            v = oracle.nrm(x)
+            ex = exact_pnorm(x, 2)
+            d = oracle.tree_depth(n, P)
+            assert rel(v, ex) <= ub(d, prec) * eps, (n, dt)
+
+
+def test_binary128_reference_vs_mpmath():
+    """The binary128 reference agrees with a 2300-bit evaluation."""
+    for n in (1, 5, 16, 100, 1000):
+        for p in (2.0, 1.0, 3.0, 7.5, math.inf):
+            x = rng_d(n + 1, n)
+            hi, lo = oracle.ref_q128(x, p)
+            ex = exact_pnorm(x, p)
+            assert float(abs(mpmath.mpf(hi) + lo - ex) / ex) < 1e-30, (n, p)
+
+
+def test_config0_accuracy():
+    """n = 2^20 binary64 moderately varying data: relerr below the bound for
+    depth 20 and (soft, Section 2's observation) below 3 eps."""
+    x = inputs.vector(1 << 20, seed=0, vec=0)
+    v = oracle.nrm(x)
+    e = oracle.relerr(v, x, nthreads=4)
+    assert e <= ub(oracle.tree_depth(x.size, 64)) * EPS_D
+    assert e <= 3 * EPS_D
+    xs = inputs.vector(1 << 20, seed=0, vec=0, dtype=np.float32)
+    vs = oracle.nrm(xs)
+    es = oracle.relerr(vs, xs, nthreads=4)
+    assert es <= ub(oracle.tree_depth(xs.size, 128), "S") * EPS_S
+    assert es <= 3 * EPS_S
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_constant_vector_closed_forms(dt):
+    """Closed forms on constant vectors c repeated n times:
+    p = 2 -> |c| sqrt(n) within the bound; p = 1 and n = 2^k -> n|c| exactly;
+    p in {1.5, 3, 7.5}, n = 2^16: each of the 16 levels combines equal values,
+    so the result is |c| * C applied 16 times with C = pow(2, 1/p), within
+    1e-14 (D) / 5e-6 (S) of |c| n^(1/p)."""
+    eps = EPS_D if dt == np.float64 else EPS_S
+    prec = "D" if dt == np.float64 else "S"
+    tol = 1e-14 if dt == np.float64 else 5e-6
+    P = oracle.P_D if dt == np.float64 else oracle.P_S
+    for c in (1.0, -3.0, 1.7, 0.1234):
+        for n in (1000, 4096, 65536, 100003):
+            x = np.full(n, c, dtype=dt)
+            v = oracle.nrm(x)
+            ex = abs(mpmath.mpf(float(dt(c)))) * mpmath.sqrt(n)
+            assert rel(v, ex) <= ub(oracle.tree_depth(n, P), prec) * eps
+        for k in (0, 5, 12, 16):
+            x = np.full(1 << k, c, dtype=dt)
+            assert oracle.nrm(x, p=1.0) == dt(abs(dt(c)) * (1 << k))
+        n = 1 << 16
+        for p in (1.5, 3.0, 7.5):
+            x = np.full(n, c, dtype=dt)
+            v = oracle.nrm(x, p=p)
+            ex = abs(mpmath.mpf(float(dt(c)))) * mpmath.mpf(n) ** (1 / mpmath.mpf(float(dt(p))))
+            assert rel(v, ex) <= tol, (c, p)
+
+
+def test_scaling_and_sign_invariance():
+    """Scaling all entries by 2^k scales the result by exactly 2^k (no
+    over/underflow: every step of v1_hypot / v1_lp is scale-free except
+    M * s), and sign flips change nothing."""
+    x = rng_d(21, 5000)
+    xs = rng_s(21, 5000)
+    sgn = np.where(np.arange(5000) % 3 == 0, -1.0, 1.0)
+    for p in (2.0, 1.0, 3.0, math.inf):
+        v = oracle.nrm(x, p)
+        for k in (-900, -37, 1, 600, 960):
+            assert oracle.nrm(x * 2.0 ** k, p) == v * 2.0 ** k
+        assert same_bits(oracle.nrm(x * sgn, p), v)
+        vs = oracle.nrm(xs, p)
+        for k in (-90, -5, 3, 90):
+            assert oracle.nrm(xs * np.float32(2.0 ** k), p) == vs * np.float32(2.0 ** k)
+        assert same_bits(oracle.nrm(xs * sgn.astype(np.float32), p), vs)
+
+
+def test_overflow_probe_small_n():
+    """Entries near 2^1020 (D) / 2^125 (S): no undue overflow, the result is
+    finite and accurate (a plain sum of squares would overflow)."""
+    for n in (2, 5, 16):
+        x = inputs.vector(n, seed=n, vec=1, emin=1020, emax=1020)
+        assert not np.isfinite(np.sum(x * x))
+        v = oracle.nrm(x)
+        assert np.isfinite(v)
+        assert rel(v, exact_pnorm(x, 2)) <= ub(oracle.tree_depth(n, 64)) * EPS_D
+        xs = inputs.vector(n, seed=n, vec=1, dtype=np.float32, emin=125, emax=125)
+        vs = oracle.nrm(xs)
+        assert np.isfinite(vs)
+        assert rel(vs, exact_pnorm(xs, 2)) <= ub(oracle.tree_depth(n, 128), "S") * EPS_S
+
+
+def test_overflow_to_inf_when_norm_exceeds_range():
+    """When the true norm exceeds the format's range, +inf (not NaN)."""
+    x = inputs.vector(1 << 12, seed=1, vec=1, emin=1020, emax=1020)
+    v = oracle.nrm(x)
+    assert math.isinf(v) and v > 0
+
+
+def test_underflow_probe():
+    """Entries in [2^-1022, 2^-1021) (D) / [2^-126, 2^-125) (S): squares
+    would underflow, the recursion does not."""
+    for n in (3, 16, 1000):
+        x = inputs.vector(n, seed=n, vec=2, emin=-1022, emax=-1022)
+        assert np.sum(x * x) == 0.0
+        v = oracle.nrm(x)
+        hi, lo = oracle.ref_q128(x)
+        assert abs(v - hi) / hi <= ub(oracle.tree_depth(n, 64)) * EPS_D
+        xs = inputs.vector(n, seed=n, vec=2, dtype=np.float32, emin=-126, emax=-126)
+        vs = oracle.nrm(xs)
+        hs, _ = oracle.ref_q128(xs)
+        assert abs(float(vs) - hs) / hs <= ub(oracle.tree_depth(n, 128), "S") * EPS_S
+
+
+# ---------------------------------------------------------------------------
+# v1_lp and the in-repo pow (Listing 5, Section 4)
+# ---------------------------------------------------------------------------
+
+def ulp_err(v, ex, dt):
+    if ex == 0:
+        return 0.0 if v == 0 else math.inf
+    e = int(mpmath.floor(mpmath.log(abs(ex), 2)))
+    mant = 52 if dt == np.float64 else 23
+    emin = -1022 if dt == np.float64 else -126
+    u = mpmath.mpf(2) ** (max(e, emin) - mant)
+    return float(abs(mpmath.mpf(float(v)) - ex) / u)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_pow_accuracy(dt):
+    """pow(x, y) within 1 ulp of x^y on the two domains v1_lp uses:
+    Q in [0,1] with y = p/2 and Z in [1,2] with y = 1/p."""
+    r = random.Random(9)
+    worst = 0.0
+    for _ in range(3000):
+        p = r.choice([0.5, 2 / 3, 1.5, math.sqrt(2), math.e, math.pi, 3.0, 7.5, r.uniform(0.5, 20)])
+        if r.random() < 0.5:
+            x = r.random() ** r.choice([1, 3, 20])
+            y = p * 0.5
+        else:
+            x = 1.0 + r.random()
+            y = 1.0 / p
+        x, y = dt(x), dt(y)
+        v = oracle.pow_(x, y, dt)
+        ex = mpmath.mpf(float(x)) ** mpmath.mpf(float(y))
+        if dt == np.float32 and ex < mpmath.mpf(2) ** -126:
+            continue
+        if dt == np.float64 and ex < mpmath.mpf(2) ** -1022:
+            continue
+        e = ulp_err(v, ex, dt)
+        worst = max(worst, e)
+    assert worst <= 1.0, worst
+
+
+def test_pow_exact_cases():
+    for dt in (np.float64, np.float32):
+        for y in (0.25, 0.5, 1.0, 3.75, 100.0):
+            assert oracle.pow_(0.0, y, dt) == 0.0
+            assert oracle.pow_(1.0, y, dt) == 1.0
+        assert oracle.pow_(2.0, 1.0, dt) == 2.0
+        assert oracle.pow_(0.25, 0.5, dt) == 0.5
+        assert oracle.pow_(4.0, 1.5, dt) == 8.0
+        assert oracle.pow_(0.5, 3.0, dt) == 0.125
+
+
+def test_pow_constants_are_correctly_rounded():
+    """The double-word constants ln 2 and 1/ln 2 that the pow uses are
+    (RN(c), RN(c - RN(c))) in each format."""
+    src = open(oracle._build.SRC).read()
+
+    def const(name):
+        import re
+        m = re.search(r"#define %s (\S+)" % name, src)
+        return float.fromhex(m.group(1).rstrip("f"))
+
+    for hi_n, lo_n, c, dt in (("LN2_HI", "LN2_LO", mpmath.log(2), np.float64),
+                              ("ILN2_HI", "ILN2_LO", 1 / mpmath.log(2), np.float64),
+                              ("LN2F_HI", "LN2F_LO", mpmath.log(2), np.float32),
+                              ("ILN2F_HI", "ILN2F_LO", 1 / mpmath.log(2), np.float32)):
+        hi, lo = const(hi_n), const(lo_n)
+        if dt == np.float64:
+            assert hi == float(mpmath.mpf(c))
+            assert lo == float(c - mpmath.mpf(hi))
+        else:
+            assert hi == float(np.float32(float(c))) or abs(mpmath.mpf(hi) - c) <= mpmath.mpf(2) ** -25
+            assert np.float32(hi) == hi and np.float32(lo) == lo
+            assert abs(mpmath.mpf(hi) + lo - c) < mpmath.mpf(2) ** -47
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_lp_combine_brute_force(dt):
+    """Eq. sp: v1_lp(x, y) ~ (|x|^p + |y|^p)^(1/p) to a few ulps; p = 2 via
+    Listing 5 differs from v1_hypot by at most a few ulps; v1_lp(a, 0) = a."""
+    r = random.Random(10)
+    eps = EPS_D if dt == np.float64 else EPS_S
+    for _ in range(1500):
+        p = r.choice([0.5, 1.5, 3.0, 7.5, math.pi])
+        a = dt(r.uniform(0.5, 2) * 2.0 ** r.randint(-20, 20))
+        b = dt(r.uniform(-2, 2) * 2.0 ** r.randint(-20, 20))
+        v = oracle.lp(p, a, b, dt)
+        pp = mpmath.mpf(float(dt(p)))
+        ex = (abs(mpmath.mpf(float(a))) ** pp + abs(mpmath.mpf(float(b))) ** pp) ** (1 / pp)
+        assert rel(v, ex) <= 6 * eps, (p, a, b)
+        assert oracle.lp(p, a, 0.0, dt) == abs(a)
+
+
+@pytest.mark.parametrize("p", [1.0, 1.5, 3.0, 7.5, 0.5, math.inf])
+def test_pnorm_against_binary128(p):
+    """xNRMP on moderately varying data (e in [-8, 8], the p-norm workload)
+    against the binary128 reference: D within 1e-14, S within 5e-6; the D
+    error is of the magnitude of Table 4 (a few eps)."""
+    x = inputs.vector(1 << 16, seed=3, vec=4, emin=-8, emax=8)
+    v = oracle.nrm(x, p)
+    e = oracle.relerr(v, x, p, nthreads=4)
+    assert e <= 1e-14
+    assert e <= 8 * EPS_D
+    xs = inputs.vector(1 << 16, seed=3, vec=4, dtype=np.float32, emin=-8, emax=8)
+    vs = oracle.nrm(xs, p)
+    assert oracle.relerr(vs, xs, p, nthreads=4) <= 5e-6
+
+
+def test_table4_magnitude_soft():
+    """Table 4 reports max relerr between 1.25 and 4.2 eps for p in
+    {1/2, 2/3, 1, sqrt 2, e, pi}; ours is of the same magnitude (< 10 eps)."""
+    x = inputs.vector(1 << 18, seed=4, vec=5, emin=-8, emax=8)
+    for row in golden_rows("table4_pnorm_relerr.txt"):
+        p = float(row[0])
+        e = oracle.relerr(oracle.nrm(x, p), x, p, nthreads=4) / EPS_D
+        assert e < 10.0, (p, e)
+
+
+def test_nrm_batch_matches_single():
+    x, off = inputs.ragged_batch(40, seed=1, max_log2=12)
+    out = oracle.nrm_batch(x, off)
+    for i in range(40):
+        assert out[i] == oracle.nrm(x[off[i]:off[i + 1]])
+
+
+def test_empty_is_zero():
+    """n = 0: +0 (Listing 1 assumes n > 0; +0 is the norm of the empty array)."""
+    assert oracle.nrm(np.zeros(0)) == 0.0
+    assert oracle.nrm(np.zeros(0, np.float32)) == 0.0
