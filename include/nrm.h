@@ -1,0 +1,208 @@
+/*
+ * nrm.h -- C ABI of the GB300 (sm_103a) library for xNRMF / xNRMP
+ * (V. Novakovic, "Recursive vectorized computation of the vector p-norm",
+ * arXiv 2509.06220).
+ *
+ * What every entry point computes
+ * -------------------------------
+ * The norm of an array x[0..n) is the paper's vectorised recursion Z
+ * (Listing 4, Section 3) with a fixed lane count P, followed by a final
+ * recursive reduction R (Listing 1) of the P lane partial norms:
+ *
+ *   rows     : row r holds x[r*P .. r*P+P), the last row zero-padded
+ *              (Listing 4's masked TAIL load); m = ceil(n/P) rows;
+ *   row tree : the rows are combined lane by lane with Listing 1's split
+ *              (left part ceil(m/2) rows, right part floor(m/2));
+ *   lanes    : the P lane results are combined by R with contiguous
+ *              pairing (lanes 2i and 2i+1 first);
+ *   combine  : p = 2 -> v1_hypot (Listing 2, the algorithm H); p = 1 ->
+ *              |x|+|y| (Eq. vp1); p = inf -> max(|x|,|y|) (Eq. vpI);
+ *              other p > 0 -> v1_lp (Listing 5) with p/2 and 1/p computed
+ *              once per call and the library's own pow.
+ *
+ * P = 64 for binary64 (the D routines) and P = 128 for binary32 (S), i.e.
+ * one 512-byte row.  Section 3 notes that the vectorised results are
+ * reproducible only for a fixed lane count; with P fixed, every result of
+ * this library is bitwise identical across launches, grid sizes, tuning
+ * parameters, batch composition, input alignment and streams.  All
+ * arithmetic is IEEE round-to-nearest-even in the input's format, with no
+ * contraction beyond the paper's explicit fma, and subnormals are kept.
+ *
+ * Conventions
+ * -----------
+ * - Pointers named x, out, offsets, status are DEVICE pointers owned by the
+ *   caller unless the name ends in _host.  Inputs must stay valid and
+ *   unmodified until the work queued on `stream` has finished.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Calls are asynchronous and stream-ordered; results stay on
+ *   the device.
+ * - A context owns device workspace (tickets and partial-norm slots) that
+ *   calls reuse.  One context may be used from one host thread at a time and
+ *   its calls must be ordered on one stream (or externally synchronised);
+ *   use one context per concurrent stream.
+ * - Argument errors are reported synchronously by the return value and
+ *   enqueue nothing.  NRM_ECUDA means a CUDA call failed; nrm_last_error()
+ *   returns its message.  No entry point traps or hangs the GPU.
+ * - Inputs are expected to be finite.  Infinite entries give +inf.  A NaN is
+ *   handled exactly as Listing 2 does (fmin/fmax return the other operand),
+ *   which this library reproduces bit for bit up to the NaN payload.
+ */
+#ifndef NRM_H
+#define NRM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef int32_t nrm_status;
+#define NRM_OK 0
+#define NRM_EINVAL (-1)   /* bad argument (NULL pointer, n < 0, p <= 0 or NaN, ...) */
+#define NRM_ENOMEM (-2)   /* device workspace could not be allocated */
+#define NRM_ECUDA (-3)    /* a CUDA runtime call failed (see nrm_last_error) */
+#define NRM_ETIMEOUT (-4) /* a bounded wait ran out */
+#define NRM_EBUDGET (-5)  /* a request can never fit the serving memory budget */
+#define NRM_EDEVICE (-6)  /* no usable CUDA device */
+
+/* Element types. */
+typedef int32_t nrm_dtype;
+#define NRM_F32 0 /* binary32, P = 128 lanes (the S routines) */
+#define NRM_F64 1 /* binary64, P = 64 lanes (the D routines) */
+
+typedef struct nrm_ctx nrm_ctx;
+
+/* Tuning knobs.  None of them changes any result bit; they only change how
+ * the fixed tree is mapped onto warps. */
+typedef struct {
+    int32_t group_log2;      /* rows loaded per warp before combining: 2^g, g in 2..3 */
+    int32_t warps_per_block; /* 4, 8 or 16 */
+    int32_t item_log2;       /* rows per warp work item: 2^k slots, k in g..g+10 */
+    int32_t blocks_per_sm;   /* persistent-grid residency target, 1..16 */
+} nrm_tuning;
+
+/* Create a context on CUDA device `device` (the device is made current on
+ * the calling thread).  *ctx receives the handle.  Returns NRM_EDEVICE if the
+ * device does not exist, NRM_ENOMEM if the initial workspace cannot be
+ * allocated. */
+nrm_status nrm_create(nrm_ctx **ctx, int device);
+
+/* Destroy a context after synchronising its device; frees its workspace and
+ * captured graphs.  NULL is accepted. */
+nrm_status nrm_destroy(nrm_ctx *ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char *nrm_status_string(nrm_status s);
+
+/* Message of the last CUDA error seen by this context ("" if none). */
+const char *nrm_last_error(const nrm_ctx *ctx);
+
+/* Ensure at least `bytes` of workspace are allocated (synchronous).  Call
+ * this before capturing library calls into a CUDA graph, since growth
+ * allocates. */
+nrm_status nrm_reserve(nrm_ctx *ctx, size_t bytes);
+
+/* Workspace bytes a call with the given shape needs under the current
+ * tuning (single vector: B = 1, x_len = n). */
+size_t nrm_workspace_bytes(const nrm_ctx *ctx, nrm_dtype dtype, int64_t x_len, int64_t B);
+
+nrm_status nrm_get_tuning(const nrm_ctx *ctx, nrm_tuning *t);
+/* Returns NRM_EINVAL (and keeps the old values) if a field is out of range. */
+nrm_status nrm_set_tuning(nrm_ctx *ctx, const nrm_tuning *t);
+
+/*
+ * xNRMF (Section 3, the recommended Z + recursive final reduction, with
+ * v1_hypot of Listing 2 at every node): *out = ||x[0..n)||_F.
+ *   x   : device pointer to n contiguous elements, any element alignment;
+ *   n   : number of elements, n >= 0; n == 0 gives +0 (Listing 1 assumes
+ *         n > 0; +0 is the norm of the empty array);
+ *   out : device pointer to one element, written asynchronously.
+ * Errors: NRM_EINVAL for ctx == NULL, out == NULL, n < 0, or x == NULL
+ * with n > 0.
+ */
+nrm_status nrmf_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *stream);
+nrm_status nrmf_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream);
+
+/*
+ * xNRMP (Section 4): *out = ||x[0..n)||_p by the same tree with the combine
+ * chosen by p: p == 2 is exactly xNRMF; p == 1 sums |x| (Eq. vp1); p == +inf
+ * takes max |x| (Eq. vpI); otherwise v1_lp (Listing 5, Eqs. sp and qp) with
+ * h = p*0.5 and ip = 1/p rounded once in the element type.  0 < p < 1 gives
+ * the quasi-norm the paper mentions.  Errors as nrmf_*, plus NRM_EINVAL for
+ * p <= 0 or p NaN.
+ */
+nrm_status nrmp_s(nrm_ctx *ctx, const float *x, int64_t n, float p, float *out, void *stream);
+nrm_status nrmp_d(nrm_ctx *ctx, const double *x, int64_t n, double p, double *out, void *stream);
+
+/*
+ * Ragged batch (the paper's per-column norms of Section 3.1, here for a
+ * batch of independent vectors): for i in [0, B),
+ *   out[i] = ||x[offsets[i] .. offsets[i+1])||_p
+ * with the same tree as nrmp_* (p is rounded to the element type first).
+ *   x       : device pointer to x_len elements of `dtype`;
+ *   offsets : device pointer to B+1 int64 element offsets (not bytes);
+ *   out     : device pointer to B elements of `dtype`;
+ *   status  : device pointer to B int32 (may be NULL): NRM_OK per vector,
+ *             or NRM_EINVAL where offsets[i] < 0, offsets[i+1] < offsets[i]
+ *             or offsets[i+1] > x_len -- that vector's out[i] is then NaN.
+ *             Bad offsets are detected on the device; nothing traps.  If
+ *             overlapping offsets would need more workspace than x_len
+ *             implies, every vector reports NRM_ENOMEM (out NaN).
+ * Work is distributed by a device-side plan and one persistent launch; every
+ * out[i] is bitwise identical to nrmp_* on that vector alone.
+ * Errors (synchronous): NRM_EINVAL for bad dtype, B < 0, x_len < 0, NULL
+ * offsets/out with B > 0, p <= 0 or NaN.
+ */
+nrm_status nrm_batch(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
+                     int64_t B, double p, void *out, int32_t *status, void *stream);
+
+/*
+ * The same batch captured once into a CUDA graph (plan kernel + tree
+ * kernel) and replayed with nrm_graph_launch; each replay reads the current
+ * contents of x and offsets.  The context's workspace is sized for x_len and
+ * B at capture time.  *graph receives an opaque handle owned by ctx.
+ */
+typedef struct nrm_graph nrm_graph;
+nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
+                           int64_t B, double p, void *out, int32_t *status, nrm_graph **graph);
+nrm_status nrm_graph_launch(nrm_graph *graph, void *stream);
+nrm_status nrm_graph_destroy(nrm_graph *graph);
+
+/*
+ * End-to-end call on HOST buffers: copies x_host[0..n) to the device in
+ * chunks that overlap with the tree computation, computes ||x||_p as
+ * nrmp_*, and copies the result to *out_host; returns when it is there.
+ * x_host may be pageable or pinned (pinned is faster).  Errors as nrmp_*.
+ */
+nrm_status nrm_host(nrm_ctx *ctx, nrm_dtype dtype, const void *x_host, int64_t n, double p, void *out_host);
+
+/*
+ * Seeded synthetic input generator (not part of the method): fills
+ * x[0..n) with elements start..start+n-1 of vector `vec` of `seed`, built
+ * bit by bit from the SplitMix64 counter hash: sign bit random, fraction
+ * uniform on the format's grid, exponent uniform in [emin, emax] (normal
+ * range of the format).  nrm_gen_ragged fills a concatenated batch of x_len
+ * elements, element j of vector i drawn from vector id i; vectors whose
+ * offsets are malformed are skipped.  Errors: NRM_EINVAL for a bad dtype,
+ * n < 0 or an exponent range outside the normal range.
+ */
+nrm_status nrm_gen(nrm_dtype dtype, void *x, int64_t n, uint64_t seed, uint64_t vec, int64_t start, int32_t emin,
+                   int32_t emax, void *stream);
+nrm_status nrm_gen_ragged(nrm_dtype dtype, void *x, int64_t x_len, const int64_t *offsets, int64_t B, uint64_t seed,
+                          int32_t emin, int32_t emax, void *stream);
+
+/* Number of tree-kernel launches this context has issued (for accounting). */
+uint64_t nrm_kernel_launches(const nrm_ctx *ctx);
+
+/* Host-side fault injection for tests (no GPU involvement): the next `count`
+ * workspace or staging allocations of any context fail with NRM_ENOMEM
+ * without calling cudaMalloc.  count <= 0 disarms it. */
+void nrm_test_inject_alloc_failures(int count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRM_H */

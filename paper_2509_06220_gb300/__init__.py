@@ -1,0 +1,336 @@
+"""GB300 (sm_103a) xNRMF / xNRMP: recursive hypot-tree norms (arXiv 2509.06220).
+
+A thin ctypes binding of the C ABI in include/nrm.h (libnrm.so, built in
+tree by ``paper_2509_06220_gb300.build``).  PyTorch provides device memory
+and streams; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library is missing the import of
+the binding raises.
+
+Entry points (same names as the C ABI):
+
+* ``nrmf(x)``           xNRMF of a 1-D float32/float64 CUDA tensor (0-d result on device)
+* ``nrmp(x, p)``        xNRMP, p > 0 (p = 2 is xNRMF, p = 1 sum |x|, p = inf max |x|)
+* ``nrm_batch(x, offsets, p)``       ragged batch -> (out, status)
+* ``nrm_batch_graph(...)``           the same, captured once as a CUDA graph
+* ``nrm_host(x_host, p)``            host buffer in, Python float out (end to end)
+* ``nrm_gen`` / ``nrm_gen_ragged``   seeded synthetic inputs on the device
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build_mod
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(HERE), "include", "nrm.h")
+
+NRM_OK, NRM_EINVAL, NRM_ENOMEM, NRM_ECUDA, NRM_ETIMEOUT, NRM_EBUDGET, NRM_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+NRM_F32, NRM_F64 = 0, 1
+P_LANES = {NRM_F32: 128, NRM_F64: 64}
+
+
+class NrmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s%s" % (_status_name(status), (": " + msg) if msg else ""))
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("group_log2", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("item_log2", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path():
+    return _build_mod.LIB
+
+
+def load():
+    """Load libnrm.so (must have been built; no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError("libnrm.so is not built (%s); run paper_2509_06220_gb300.build.build() or "
+                          "__graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, i64, i32, u64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_size_t
+    st = ctypes.c_int32
+    sigs = {
+        "nrm_create": (st, [ctypes.POINTER(vp), ctypes.c_int]),
+        "nrm_destroy": (st, [vp]),
+        "nrm_status_string": (ctypes.c_char_p, [st]),
+        "nrm_last_error": (ctypes.c_char_p, [vp]),
+        "nrm_reserve": (st, [vp, sz]),
+        "nrm_workspace_bytes": (sz, [vp, i32, i64, i64]),
+        "nrm_get_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
+        "nrm_set_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
+        "nrmf_s": (st, [vp, vp, i64, vp, vp]),
+        "nrmf_d": (st, [vp, vp, i64, vp, vp]),
+        "nrmp_s": (st, [vp, vp, i64, ctypes.c_float, vp, vp]),
+        "nrmp_d": (st, [vp, vp, i64, ctypes.c_double, vp, vp]),
+        "nrm_batch": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, vp]),
+        "nrm_batch_graph": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, ctypes.POINTER(vp)]),
+        "nrm_graph_launch": (st, [vp, vp]),
+        "nrm_graph_destroy": (st, [vp]),
+        "nrm_host": (st, [vp, i32, vp, i64, ctypes.c_double, vp]),
+        "nrm_gen": (st, [i32, vp, i64, u64, u64, i64, i32, i32, vp]),
+        "nrm_gen_ragged": (st, [i32, vp, i64, vp, i64, u64, i32, i32, vp]),
+        "nrm_kernel_launches": (u64, [vp]),
+        "nrm_test_inject_alloc_failures": (None, [ctypes.c_int]),
+    }
+    for name, (res, args) in sigs.items():
+        if hasattr(L, name):
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of the functions include/nrm.h declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(nrm\w*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def _status_name(s):
+    try:
+        return load().nrm_status_string(s).decode()
+    except Exception:
+        return "status %d" % s
+
+
+# ---------------------------------------------------------------------------
+# contexts
+# ---------------------------------------------------------------------------
+
+class Context:
+    """Owns an nrm_ctx (device workspace, tuning, captured graphs)."""
+
+    def __init__(self, device=0):
+        L = load()
+        h = ctypes.c_void_p()
+        s = L.nrm_create(ctypes.byref(h), int(device))
+        if s != NRM_OK:
+            raise NrmError(s, "nrm_create(device=%d)" % device)
+        self.h = h
+        self.device = device
+        self._graphs = []
+
+    def close(self):
+        if self.h:
+            load().nrm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, s, what):
+        if s != NRM_OK:
+            msg = load().nrm_last_error(self.h).decode() if self.h else ""
+            raise NrmError(s, "%s %s" % (what, msg))
+
+    @property
+    def tuning(self):
+        t = Tuning()
+        self.check(load().nrm_get_tuning(self.h, ctypes.byref(t)), "nrm_get_tuning")
+        return t
+
+    def set_tuning(self, group_log2=None, warps_per_block=None, item_log2=None, blocks_per_sm=None):
+        t = self.tuning
+        for k, v in (("group_log2", group_log2), ("warps_per_block", warps_per_block),
+                     ("item_log2", item_log2), ("blocks_per_sm", blocks_per_sm)):
+            if v is not None:
+                setattr(t, k, int(v))
+        self.check(load().nrm_set_tuning(self.h, ctypes.byref(t)), "nrm_set_tuning")
+
+    def reserve(self, nbytes):
+        self.check(load().nrm_reserve(self.h, int(nbytes)), "nrm_reserve")
+
+    def workspace_bytes(self, dtype, x_len, B=1):
+        return load().nrm_workspace_bytes(self.h, dtype, int(x_len), int(B))
+
+    @property
+    def launches(self):
+        return load().nrm_kernel_launches(self.h)
+
+
+_ctxs = {}
+
+
+def context(device=None):
+    import torch
+    if device is None:
+        device = torch.cuda.current_device()
+    if isinstance(device, torch.device):
+        device = device.index if device.index is not None else torch.cuda.current_device()
+    c = _ctxs.get(device)
+    if c is None:
+        c = _ctxs[device] = Context(device)
+    return c
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return NRM_F64
+    if t.dtype == torch.float32:
+        return NRM_F32
+    raise TypeError("float32 or float64 tensor required, got %s" % t.dtype)
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_vec(x):
+    if not x.is_cuda:
+        raise ValueError("x must be a CUDA tensor")
+    if x.dim() != 1 or (x.numel() > 1 and x.stride(0) != 1):
+        raise ValueError("x must be a contiguous 1-D tensor")
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+
+def nrmp(x, p=2.0, out=None, stream=None, ctx=None):
+    """||x||_p of a contiguous 1-D CUDA tensor by the fixed hypot tree."""
+    import torch
+    _check_vec(x)
+    dt = _dtype_code(x)
+    c = ctx or context(x.device)
+    if out is None:
+        out = torch.empty((), dtype=x.dtype, device=x.device)
+    L = load()
+    xp = ctypes.c_void_p(x.data_ptr() if x.numel() else 0)
+    op = ctypes.c_void_p(out.data_ptr())
+    s = _stream(stream)
+    if dt == NRM_F64:
+        r = L.nrmf_d(c.h, xp, x.numel(), op, s) if p == 2.0 else L.nrmp_d(c.h, xp, x.numel(), float(p), op, s)
+    else:
+        r = L.nrmf_s(c.h, xp, x.numel(), op, s) if p == 2.0 else L.nrmp_s(c.h, xp, x.numel(), float(p), op, s)
+    c.check(r, "nrm%s_%s" % ("f" if p == 2.0 else "p", "d" if dt == NRM_F64 else "s"))
+    return out
+
+
+def nrmf(x, out=None, stream=None, ctx=None):
+    """xNRMF: the Frobenius norm by the recursive v1_hypot tree."""
+    return nrmp(x, 2.0, out, stream, ctx)
+
+
+def nrm_batch(x, offsets, p=2.0, out=None, status=None, stream=None, ctx=None):
+    """Norms of x[offsets[i]:offsets[i+1]] for all i; returns (out, status)."""
+    import torch
+    _check_vec(x)
+    dt = _dtype_code(x)
+    if offsets.dtype != torch.int64 or not offsets.is_cuda or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+    B = offsets.numel() - 1
+    c = ctx or context(x.device)
+    if out is None:
+        out = torch.empty(max(B, 0), dtype=x.dtype, device=x.device)
+    if status is None:
+        status = torch.empty(max(B, 0), dtype=torch.int32, device=x.device)
+    r = load().nrm_batch(c.h, dt, ctypes.c_void_p(x.data_ptr() if x.numel() else 0), x.numel(),
+                         ctypes.c_void_p(offsets.data_ptr()), B, float(p), ctypes.c_void_p(out.data_ptr()),
+                         ctypes.c_void_p(status.data_ptr()), _stream(stream))
+    c.check(r, "nrm_batch")
+    return out, status
+
+
+class BatchGraph:
+    """A ragged batch captured once as a CUDA graph (plan + tree kernel)."""
+
+    def __init__(self, x, offsets, p=2.0, out=None, status=None, ctx=None):
+        import torch
+        _check_vec(x)
+        dt = _dtype_code(x)
+        B = offsets.numel() - 1
+        self.ctx = ctx or context(x.device)
+        self.x, self.offsets = x, offsets
+        self.out = out if out is not None else torch.empty(B, dtype=x.dtype, device=x.device)
+        self.status = status if status is not None else torch.empty(B, dtype=torch.int32, device=x.device)
+        h = ctypes.c_void_p()
+        r = load().nrm_batch_graph(self.ctx.h, dt, ctypes.c_void_p(x.data_ptr()), x.numel(),
+                                   ctypes.c_void_p(offsets.data_ptr()), B, float(p),
+                                   ctypes.c_void_p(self.out.data_ptr()), ctypes.c_void_p(self.status.data_ptr()),
+                                   ctypes.byref(h))
+        self.ctx.check(r, "nrm_batch_graph")
+        self.h = h
+
+    def launch(self, stream=None):
+        self.ctx.check(load().nrm_graph_launch(self.h, _stream(stream)), "nrm_graph_launch")
+        return self.out, self.status
+
+    def close(self):
+        if self.h:
+            load().nrm_graph_destroy(self.h)
+            self.h = None
+
+
+def nrm_batch_graph(x, offsets, p=2.0, out=None, status=None, ctx=None):
+    return BatchGraph(x, offsets, p, out, status, ctx)
+
+
+def nrm_host(x_host, p=2.0, ctx=None, device=0):
+    """End to end: host array in (numpy or CPU tensor, ideally pinned), the
+    norm as a Python float out; host->device copies overlap the tree."""
+    import torch
+    if isinstance(x_host, np.ndarray):
+        a = np.ascontiguousarray(x_host)
+        ptr, n, isd = a.ctypes.data, a.size, a.dtype == np.float64
+        if a.dtype not in (np.float64, np.float32):
+            raise TypeError("float32 or float64 required")
+    else:
+        if x_host.is_cuda or not x_host.is_contiguous():
+            raise ValueError("x_host must be a contiguous CPU tensor")
+        ptr, n, isd = x_host.data_ptr(), x_host.numel(), x_host.dtype == torch.float64
+    dt = NRM_F64 if isd else NRM_F32
+    c = ctx or context(device)
+    res = (ctypes.c_double if isd else ctypes.c_float)()
+    r = load().nrm_host(c.h, dt, ctypes.c_void_p(ptr), n, float(p), ctypes.byref(res))
+    c.check(r, "nrm_host")
+    return res.value
+
+
+def nrm_gen(n, seed=0, vec=0, dtype=None, emin=-20, emax=20, start=0, device=None, out=None, stream=None):
+    """Seeded synthetic vector on the device (same definition as inputs.vector)."""
+    import torch
+    dtype = dtype or torch.float64
+    if out is None:
+        out = torch.empty(n, dtype=dtype, device=device or "cuda")
+    dt = _dtype_code(out)
+    r = load().nrm_gen(dt, ctypes.c_void_p(out.data_ptr() if n else 0), int(n), int(seed) & (2 ** 64 - 1),
+                       int(vec) & (2 ** 64 - 1), int(start), int(emin), int(emax), _stream(stream))
+    if r != NRM_OK:
+        raise NrmError(r, "nrm_gen")
+    return out
+
+
+def nrm_gen_ragged(offsets, seed=0, dtype=None, emin=-20, emax=20, out=None, stream=None):
+    import torch
+    dtype = dtype or torch.float64
+    n = int(offsets[-1].item())
+    if out is None:
+        out = torch.empty(n, dtype=dtype, device=offsets.device)
+    dt = _dtype_code(out)
+    r = load().nrm_gen_ragged(dt, ctypes.c_void_p(out.data_ptr() if n else 0), out.numel(),
+                              ctypes.c_void_p(offsets.data_ptr()), offsets.numel() - 1, int(seed) & (2 ** 64 - 1),
+                              int(emin), int(emax), _stream(stream))
+    if r != NRM_OK:
+        raise NrmError(r, "nrm_gen_ragged")
+    return out

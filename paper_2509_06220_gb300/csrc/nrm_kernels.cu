@@ -1,0 +1,624 @@
+// nrm_kernels.cu -- xNRMF / xNRMP tree kernels for sm_103a and the C ABI
+// declared in include/nrm.h (arXiv 2509.06220, Listings 1, 2, 4, 5).
+//
+// Mapping of the paper's vectorised recursion onto the GPU
+// ---------------------------------------------------------
+// * A vector's elements form rows of P lanes (P = 64 for binary64, 128 for
+//   binary32; one 512-byte row).  One warp holds one row in registers: thread
+//   t owns lanes [V t, V t + V), loaded with one 16-byte load.
+// * The ceil-split tree over the m rows (Listing 4's recursion on vectors)
+//   is embedded in a perfect tree of depth D = ceil(lg m): slot j holds a
+//   row iff brev_D(j) < m; a node with an empty child passes the other
+//   through, so the embedding computes exactly Listing 4's tree.
+// * The tree is cut at depth dw into 2^dw work items; a warp evaluates one
+//   item (a subtree of 2^k slots) with groups of 2^G slots combined in
+//   registers and a binary-counter stack above them.
+// * Above the cut, each internal node has a ticket.  The warp that finishes a
+//   child stores its 512-byte row of partial norms, fences, and increments
+//   the parent's ticket; the second arriver combines the two children (left
+//   operand = left child) and climbs on.  Whoever combines the root reduces
+//   the P lanes with R's contiguous pairing (in-thread, then warp shuffles)
+//   and writes the result.  The arrival order never changes a bit.
+// * The second arriver resets the ticket, so tickets are zero between calls.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nrm.h"
+#include "nrm_device.cuh"
+#include "nrm_internal.h"
+
+namespace nrm {
+
+// ---------------------------------------------------------------------------
+// kernel arguments
+// ---------------------------------------------------------------------------
+template <typename T> struct TreeArgs {
+    const T *x;
+    T *out;
+    const VecPlan *plans; // batch: device plans; nullptr: single vector `one`
+    VecPlan one;
+    int64_t B;
+    int64_t item_lo, item_hi;      // single vector: item range of this launch
+    const int64_t *total_items;    // batch: written by the plan kernel
+    unsigned long long *cursor;    // batch: dynamic work cursor (zeroed by plan)
+    unsigned *tickets;
+    T *slots;
+};
+
+// R over the P lanes held by the warp (Listing 1 with contiguous pairing):
+// first inside the thread, then across threads by xor-shuffles.
+template <typename T, class Op>
+__device__ __forceinline__ T lane_reduce(const T (&r)[Geo<T>::V], const Op &op, int lane) {
+    T v;
+    if constexpr (Geo<T>::V == 2) {
+        v = op(r[0], r[1]);
+    } else {
+        v = op(op(r[0], r[1]), op(r[2], r[3]));
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T o = __shfl_xor_sync(FULL, v, off);
+        v = (lane & off) ? op(o, v) : op(v, o);
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row(T *dst, const T (&r)[Geo<T>::V]) {
+    if constexpr (Geo<T>::V == 2) {
+        __stcg(reinterpret_cast<double2 *>(dst), make_double2(r[0], r[1]));
+    } else {
+        __stcg(reinterpret_cast<float4 *>(dst), make_float4(r[0], r[1], r[2], r[3]));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_slot(const T *src, T (&r)[Geo<T>::V]) {
+    if constexpr (Geo<T>::V == 2) {
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(src));
+        r[0] = v.x;
+        r[1] = v.y;
+    } else {
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(src));
+        r[0] = v.x;
+        r[1] = v.y;
+        r[2] = v.z;
+        r[3] = v.w;
+    }
+}
+
+template <typename T, int G, class Op>
+__global__ void __launch_bounds__(512) tree_kernel(TreeArgs<T> a, Op op) {
+    constexpr int V = Geo<T>::V;
+    constexpr int P = Geo<T>::P;
+    const int lane = threadIdx.x & 31;
+    const int64_t wglobal = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool batch = a.plans != nullptr;
+    const int64_t total = batch ? *a.total_items : a.item_hi;
+    extern __shared__ __align__(16) unsigned char nrm_smem[];
+    T *stk = reinterpret_cast<T *>(nrm_smem) + (threadIdx.x >> 5) * (MAXL * P);
+
+    int64_t gi;
+    if (batch) {
+        unsigned long long g0 = 0;
+        if (lane == 0) g0 = atomicAdd(a.cursor, 1ull);
+        gi = (int64_t)__shfl_sync(FULL, g0, 0);
+    } else {
+        gi = a.item_lo + wglobal;
+    }
+    while (gi < total) {
+        // locate the vector owning global item gi
+        int64_t v = 0;
+        VecPlan pl;
+        if (batch) {
+            int64_t lo = 0, hi = a.B; // last v with item_base <= gi
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (a.plans[mid].item_base <= gi) lo = mid;
+                else hi = mid;
+            }
+            v = lo;
+            pl = a.plans[v];
+        } else {
+            pl = a.one;
+        }
+        const T *xv = a.x + pl.x_off;
+        const bool aligned = ((uintptr_t)xv & 15u) == 0;
+        const uint32_t i = (uint32_t)(gi - pl.item_base);
+        const int64_t t = node_rows(pl.m, i, pl.dw);
+        const int64_t start = node_start(pl.m, i, pl.dw);
+        T r[V];
+        item_tree<T, G, Op>(xv, pl.n, start, t, pl.k, lane, aligned, op, stk, r);
+
+        // climb the ticket tree above the cut
+        uint32_t h = (1u << pl.dw) + i;
+        bool root = true;
+        while (h > 1) {
+            T *mine = a.slots + ((size_t)(2 * pl.node_base + h - 2) * P) + lane * V;
+            store_row<T>(mine, r);
+            __threadfence();
+            __syncwarp();
+            unsigned tk = 0;
+            unsigned *ticket = a.tickets + (pl.node_base + (h >> 1) - 1);
+            if (lane == 0) tk = atomicAdd(ticket, 1u);
+            tk = __shfl_sync(FULL, tk, 0);
+            if (tk == 0) {
+                root = false; // the sibling is still running; it climbs on
+                break;
+            }
+            if (lane == 0) atomicExch(ticket, 0u);
+            __threadfence();
+            T sib[V];
+            load_slot<T>(a.slots + ((size_t)(2 * pl.node_base + (h ^ 1u) - 2) * P) + lane * V, sib);
+            if (h & 1u) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) r[j] = op(sib[j], r[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) r[j] = op(r[j], sib[j]);
+            }
+            h >>= 1;
+        }
+        if (root) {
+            const T res = lane_reduce<T, Op>(r, op, lane);
+            if (lane == 0) a.out[v] = res;
+        }
+        if (batch) {
+            unsigned long long g1 = 0;
+            if (lane == 0) g1 = atomicAdd(a.cursor, 1ull);
+            gi = (int64_t)__shfl_sync(FULL, g1, 0);
+        } else {
+            gi += nwarps;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batch planning (one block): offsets -> per-vector plans, prefix sums of
+// work items and ticket nodes, statuses, outputs of empty / bad vectors, and
+// the reset of the work cursor
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ off, int64_t B, int64_t x_len,
+                                                    int kitem, int dwmax, int kmax, int64_t node_cap,
+                                                    VecPlan *plans, int64_t *totals, unsigned long long *cursor,
+                                                    T *out, int32_t *status) {
+    constexpr int P = Geo<T>::P;
+    __shared__ int64_t s_items[1024], s_nodes[1024];
+    const int tid = threadIdx.x;
+    const int64_t per = (B + blockDim.x - 1) / blockDim.x;
+    const int64_t v0 = min(B, tid * per), v1 = min(B, v0 + per);
+    auto plan_of = [&](int64_t v, VecPlan &pl, int64_t &items, int64_t &nodes, int32_t &st) {
+        const int64_t a = off[v], b = off[v + 1];
+        pl = VecPlan{};
+        items = 0;
+        nodes = 0;
+        st = NRM_OK;
+        if (a < 0 || b < a || b > x_len) {
+            st = NRM_EINVAL;
+            return;
+        }
+        const int64_t n = b - a;
+        pl.x_off = a;
+        pl.n = n;
+        if (n == 0) return;
+        pl.m = (n + P - 1) / P;
+        pl.D = ceil_log2_i64(pl.m);
+        int k = min(pl.D, kitem);
+        if (pl.D - k > dwmax) k = pl.D - dwmax;
+        if (k > kmax) {
+            st = NRM_EINVAL; // larger than the tree kernel supports (> 2^35 rows)
+            return;
+        }
+        pl.k = k;
+        pl.dw = pl.D - k;
+        items = int64_t(1) << pl.dw;
+        nodes = items - 1;
+    };
+    int64_t si = 0, sn = 0;
+    for (int64_t v = v0; v < v1; ++v) {
+        VecPlan pl;
+        int64_t it, nd;
+        int32_t st;
+        plan_of(v, pl, it, nd, st);
+        si += it;
+        sn += nd;
+    }
+    s_items[tid] = si;
+    s_nodes[tid] = sn;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the 1024 partial sums
+    for (int d = 1; d < 1024; d <<= 1) {
+        int64_t ai = 0, an = 0;
+        if (tid >= d) {
+            ai = s_items[tid - d];
+            an = s_nodes[tid - d];
+        }
+        __syncthreads();
+        s_items[tid] += ai;
+        s_nodes[tid] += an;
+        __syncthreads();
+    }
+    // Offsets that are individually valid but overlap (a decreasing pair in
+    // between) can need more ticket nodes than the workspace was sized for
+    // from x_len; then no vector is computed and all report NRM_ENOMEM.
+    const bool overflow = s_nodes[blockDim.x - 1] > node_cap;
+    int64_t ib = s_items[tid] - si, nb = s_nodes[tid] - sn;
+    for (int64_t v = v0; v < v1; ++v) {
+        VecPlan pl;
+        int64_t it, nd;
+        int32_t st;
+        plan_of(v, pl, it, nd, st);
+        if (overflow && st == NRM_OK) st = NRM_ENOMEM;
+        pl.item_base = ib;
+        pl.node_base = nb;
+        plans[v] = pl;
+        if (status) status[v] = st;
+        if (st != NRM_OK) out[v] = T(NAN);
+        else if (pl.n == 0) out[v] = T(0);
+        ib += it;
+        nb += nd;
+    }
+    if (tid == blockDim.x - 1) {
+        totals[0] = overflow ? 0 : s_items[tid];
+        totals[1] = s_nodes[tid];
+        *cursor = 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+constexpr int DW_MAX = 20;
+
+template <typename T> constexpr int P_of() { return Geo<T>::P; }
+
+struct Layout {
+    size_t tickets, slots, plans, totals, cursor, end;
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+static Layout layout_for(int64_t nodes, int64_t B) {
+    Layout L;
+    L.tickets = 0;
+    L.slots = align256(sizeof(unsigned) * (size_t)std::max<int64_t>(nodes, 1));
+    L.plans = L.slots + align256(512 * (size_t)std::max<int64_t>(2 * nodes, 1));
+    L.totals = L.plans + align256(sizeof(VecPlan) * (size_t)std::max<int64_t>(B, 1));
+    L.cursor = L.totals + 256;
+    L.end = L.cursor + 256;
+    return L;
+}
+
+} // namespace nrm
+
+using namespace nrm;
+
+// context --------------------------------------------------------------------
+
+static nrm_status set_cuda_err(nrm_ctx *c, cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return NRM_OK;
+    if (c) {
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    if (e == cudaErrorMemoryAllocation) return NRM_ENOMEM;
+    return NRM_ECUDA;
+}
+
+nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes) {
+    if (bytes <= c->ws_bytes) return NRM_OK;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return set_cuda_err(c, e, "cudaSetDevice");
+    if (c->ws) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return set_cuda_err(c, e, "cudaDeviceSynchronize");
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    if (nrm_test_fail_alloc()) return NRM_ENOMEM;
+    e = cudaMalloc(&c->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->ws = nullptr;
+        return set_cuda_err(c, e, "cudaMalloc(workspace)");
+    }
+    e = cudaMemset(c->ws, 0, want); // tickets start at zero
+    if (e != cudaSuccess) return set_cuda_err(c, e, "cudaMemset(workspace)");
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_cuda_err(c, e, "cudaDeviceSynchronize");
+    c->ws_bytes = want;
+    return NRM_OK;
+}
+
+extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
+    if (!ctx) return NRM_EINVAL;
+    *ctx = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return NRM_EDEVICE;
+    }
+    nrm_ctx *c = new nrm_ctx();
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return NRM_EDEVICE;
+    }
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, device);
+    c->sms = prop.multiProcessorCount;
+    c->tune = nrm_tuning{3, 8, 7, 4};
+    nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20);
+    if (s != NRM_OK) {
+        delete c;
+        return s;
+    }
+    *ctx = c;
+    return NRM_OK;
+}
+
+extern "C" nrm_status nrm_destroy(nrm_ctx *ctx) {
+    if (!ctx) return NRM_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (nrm_graph *g : ctx->graphs) nrm_graph_free(g);
+    ctx->graphs.clear();
+    nrm_host_free(ctx);
+    if (ctx->ws) cudaFree(ctx->ws);
+    delete ctx;
+    return NRM_OK;
+}
+
+extern "C" const char *nrm_status_string(nrm_status s) {
+    switch (s) {
+    case NRM_OK: return "NRM_OK";
+    case NRM_EINVAL: return "NRM_EINVAL";
+    case NRM_ENOMEM: return "NRM_ENOMEM";
+    case NRM_ECUDA: return "NRM_ECUDA";
+    case NRM_ETIMEOUT: return "NRM_ETIMEOUT";
+    case NRM_EBUDGET: return "NRM_EBUDGET";
+    case NRM_EDEVICE: return "NRM_EDEVICE";
+    default: return "NRM_UNKNOWN";
+    }
+}
+
+extern "C" const char *nrm_last_error(const nrm_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+extern "C" nrm_status nrm_reserve(nrm_ctx *ctx, size_t bytes) {
+    if (!ctx) return NRM_EINVAL;
+    return nrm_ctx_ensure(ctx, bytes);
+}
+
+extern "C" nrm_status nrm_get_tuning(const nrm_ctx *ctx, nrm_tuning *t) {
+    if (!ctx || !t) return NRM_EINVAL;
+    *t = ctx->tune;
+    return NRM_OK;
+}
+
+extern "C" nrm_status nrm_set_tuning(nrm_ctx *ctx, const nrm_tuning *t) {
+    if (!ctx || !t) return NRM_EINVAL;
+    if (t->group_log2 < 2 || t->group_log2 > 3) return NRM_EINVAL;
+    if (t->warps_per_block != 4 && t->warps_per_block != 8 && t->warps_per_block != 16) return NRM_EINVAL;
+    if (t->item_log2 < t->group_log2 || t->item_log2 > t->group_log2 + MAXL) return NRM_EINVAL;
+    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 16) return NRM_EINVAL;
+    ctx->tune = *t;
+    return NRM_OK;
+}
+
+extern "C" uint64_t nrm_kernel_launches(const nrm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+// single-vector planning ------------------------------------------------------
+
+// Plan of one vector of n elements with P lanes: cut depth dw so that there
+// are enough work items to fill the GPU (at least min_items when the tree is
+// deep enough) but items no smaller than 2^G rows and no more than 2^DW_MAX.
+static bool plan_single(const nrm_ctx *c, int64_t n, int P, VecPlan &pl) {
+    pl = VecPlan{};
+    pl.n = n;
+    pl.m = (n + P - 1) / P;
+    pl.D = ceil_log2_i64(pl.m);
+    const int G = c->tune.group_log2;
+    const int64_t min_items = (int64_t)c->sms * c->tune.warps_per_block * 2;
+    int dw_fill = ceil_log2_i64(min_items);
+    int dw = std::max(pl.D - c->tune.item_log2, dw_fill);
+    dw = std::min(dw, pl.D - G);
+    dw = std::max(dw, 0);
+    dw = std::min(dw, DW_MAX);
+    int k = pl.D - dw;
+    if (k > G + MAXL) return false;
+    pl.k = k;
+    pl.dw = dw;
+    return true;
+}
+
+template <typename T, class Op>
+static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, int64_t grid_warps,
+                               cudaStream_t s) {
+    const int wpb = c->tune.warps_per_block;
+    const size_t smem = (size_t)wpb * MAXL * 512; // per-warp counter stacks
+    int occ = 0;
+    int64_t blocks = 0;
+    cudaError_t e = cudaSuccess;
+    switch (c->tune.group_log2) {
+#define NRM_LAUNCH_G(GG)                                                                                    \
+    case GG: {                                                                                              \
+        cudaFuncSetAttribute(tree_kernel<T, GG, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<T, GG, Op>, wpb * 32, smem);       \
+        occ = std::max(1, std::min(occ, c->tune.blocks_per_sm));                                            \
+        blocks = std::max<int64_t>(1, std::min<int64_t>((grid_warps + wpb - 1) / wpb, (int64_t)c->sms * occ)); \
+        tree_kernel<T, GG, Op><<<(unsigned)blocks, wpb * 32, smem, s>>>(a, op);                             \
+        e = cudaGetLastError();                                                                             \
+        break;                                                                                              \
+    }
+        NRM_LAUNCH_G(2)
+        NRM_LAUNCH_G(3)
+#undef NRM_LAUNCH_G
+    default: return cudaErrorInvalidValue;
+    }
+    c->launches++;
+    return e;
+}
+
+// p -> combine op dispatch (Section 4): 2 -> v1_hypot, 1 -> sumabs,
+// inf -> maxabs, other -> v1_lp with p/2 and 1/p rounded once in T.
+template <typename T, class F> static cudaError_t with_op(T p, F &&f) {
+    if (p == T(2)) return f(OpHypot<T>{});
+    if (p == T(1)) return f(OpSumAbs<T>{});
+    if (std::isinf(p)) return f(OpMaxAbs<T>{});
+    OpLp<T> o;
+    o.h = p * T(0.5);
+    o.ip = T(1) / p;
+    return f(o);
+}
+
+template <typename T>
+static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cudaStream_t s, int64_t item_lo,
+                             int64_t item_hi, const VecPlan *plan_in) {
+    VecPlan pl;
+    if (plan_in) pl = *plan_in;
+    else if (!plan_single(c, n, P_of<T>(), pl)) return NRM_EINVAL;
+    const int64_t items = int64_t(1) << pl.dw;
+    const int64_t nodes = items - 1;
+    Layout L = layout_for(nodes, 1);
+    nrm_status st = nrm_ctx_ensure(c, L.end);
+    if (st != NRM_OK) return st;
+    TreeArgs<T> a{};
+    a.x = x;
+    a.out = out;
+    a.plans = nullptr;
+    a.one = pl;
+    a.B = 1;
+    a.item_lo = plan_in ? item_lo : 0;
+    a.item_hi = plan_in ? item_hi : items;
+    a.total_items = nullptr;
+    a.cursor = nullptr;
+    a.tickets = reinterpret_cast<unsigned *>((char *)c->ws + L.tickets);
+    a.slots = reinterpret_cast<T *>((char *)c->ws + L.slots);
+    const int64_t warps = a.item_hi - a.item_lo;
+    cudaError_t e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, warps, s); });
+    return set_cuda_err(c, e, "tree_kernel launch");
+}
+
+nrm_status nrm_plan_single(const nrm_ctx *c, nrm_dtype dt, int64_t n, VecPlan *pl) {
+    return plan_single(c, n, dt == NRM_F64 ? 64 : 128, *pl) ? NRM_OK : NRM_EINVAL;
+}
+
+nrm_status nrm_run_single_range(nrm_ctx *c, nrm_dtype dt, const void *x, int64_t n, double p, void *out,
+                                cudaStream_t s, const VecPlan *pl, int64_t item_lo, int64_t item_hi) {
+    if (dt == NRM_F64)
+        return run_single<double>(c, (const double *)x, n, p, (double *)out, s, item_lo, item_hi, pl);
+    return run_single<float>(c, (const float *)x, n, (float)p, (float *)out, s, item_lo, item_hi, pl);
+}
+
+template <typename T> static nrm_status check_args(nrm_ctx *c, const T *x, int64_t n, T p, T *out) {
+    if (!c || !out || n < 0 || (n > 0 && !x)) return NRM_EINVAL;
+    if (!(p > T(0))) return NRM_EINVAL; // also rejects NaN
+    return NRM_OK;
+}
+
+template <typename T> static nrm_status nrm_entry(nrm_ctx *c, const T *x, int64_t n, T p, T *out, void *stream) {
+    nrm_status st = check_args<T>(c, x, n, p, out);
+    if (st != NRM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return set_cuda_err(c, cudaMemsetAsync(out, 0, sizeof(T), s), "cudaMemsetAsync");
+    return run_single<T>(c, x, n, p, out, s, 0, 0, nullptr);
+}
+
+extern "C" nrm_status nrmf_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *stream) {
+    return nrm_entry<float>(ctx, x, n, 2.0f, out, stream);
+}
+extern "C" nrm_status nrmf_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream) {
+    return nrm_entry<double>(ctx, x, n, 2.0, out, stream);
+}
+extern "C" nrm_status nrmp_s(nrm_ctx *ctx, const float *x, int64_t n, float p, float *out, void *stream) {
+    return nrm_entry<float>(ctx, x, n, p, out, stream);
+}
+extern "C" nrm_status nrmp_d(nrm_ctx *ctx, const double *x, int64_t n, double p, double *out, void *stream) {
+    return nrm_entry<double>(ctx, x, n, p, out, stream);
+}
+
+// batch -----------------------------------------------------------------------
+
+static int64_t batch_nodes_bound(const nrm_ctx *c, int64_t x_len, int64_t B, int P) {
+    // sum over vectors of 2^dw - 1 < 2 (m_v / 2^k) summed, m_v <= n_v/P + 1
+    const int k = c->tune.item_log2;
+    const int64_t rows = x_len / P + B + 1;
+    return (2 * rows >> k) + 2;
+}
+
+size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B) {
+    const int P = dt == NRM_F64 ? 64 : 128;
+    return layout_for(batch_nodes_bound(c, x_len, B, P), B).end;
+}
+
+extern "C" size_t nrm_workspace_bytes(const nrm_ctx *ctx, nrm_dtype dtype, int64_t x_len, int64_t B) {
+    if (!ctx) return 0;
+    if (B <= 1) {
+        VecPlan pl;
+        if (!plan_single(ctx, std::max<int64_t>(x_len, 1), dtype == NRM_F64 ? 64 : 128, pl)) return 0;
+        return layout_for((int64_t(1) << pl.dw) - 1, 1).end;
+    }
+    return nrm_batch_ws_bytes(ctx, dtype, x_len, B);
+}
+
+template <typename T>
+static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t *off, int64_t B, T p, T *out,
+                            int32_t *status, cudaStream_t s) {
+    constexpr int P = Geo<T>::P;
+    const int64_t nodes_bound = batch_nodes_bound(c, x_len, B, P);
+    Layout L = layout_for(nodes_bound, B);
+    nrm_status st = nrm_ctx_ensure(c, L.end);
+    if (st != NRM_OK) return st;
+    char *ws = (char *)c->ws;
+    VecPlan *plans = reinterpret_cast<VecPlan *>(ws + L.plans);
+    int64_t *totals = reinterpret_cast<int64_t *>(ws + L.totals);
+    unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + L.cursor);
+    const int kmax = c->tune.group_log2 + MAXL;
+    plan_kernel<T><<<1, 1024, 0, s>>>(off, B, x_len, c->tune.item_log2, DW_MAX, kmax, nodes_bound, plans, totals,
+                                      cursor, out, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_err(c, e, "plan_kernel launch");
+    TreeArgs<T> a{};
+    a.x = x;
+    a.out = out;
+    a.plans = plans;
+    a.B = B;
+    a.total_items = totals;
+    a.cursor = cursor;
+    a.tickets = reinterpret_cast<unsigned *>(ws + L.tickets);
+    a.slots = reinterpret_cast<T *>(ws + L.slots);
+    const int64_t persistent = (int64_t)c->sms * 64 * c->tune.warps_per_block; // capped by occupancy
+    e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, persistent, s); });
+    return set_cuda_err(c, e, "tree_kernel launch (batch)");
+}
+
+nrm_status nrm_batch_impl(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
+                          int64_t B, double p, void *out, int32_t *status, cudaStream_t s) {
+    if (!ctx || B < 0 || x_len < 0 || (dtype != NRM_F32 && dtype != NRM_F64)) return NRM_EINVAL;
+    if (B > 0 && (!offsets || !out)) return NRM_EINVAL;
+    if (x_len > 0 && !x) return NRM_EINVAL;
+    if (!(p > 0.0)) return NRM_EINVAL;
+    if (B == 0) return NRM_OK;
+    if (dtype == NRM_F64)
+        return run_batch<double>(ctx, (const double *)x, x_len, offsets, B, p, (double *)out, status, s);
+    const float pf = (float)p;
+    if (!(pf > 0.0f)) return NRM_EINVAL;
+    return run_batch<float>(ctx, (const float *)x, x_len, offsets, B, pf, (float *)out, status, s);
+}
+
+extern "C" nrm_status nrm_batch(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len,
+                                const int64_t *offsets, int64_t B, double p, void *out, int32_t *status,
+                                void *stream) {
+    return nrm_batch_impl(ctx, dtype, x, x_len, offsets, B, p, out, status, (cudaStream_t)stream);
+}

@@ -1,0 +1,197 @@
+// nrm_runtime.cu -- host runtime around the tree kernels: CUDA-graph capture
+// of the ragged batch, the end-to-end call on host buffers (chunked copies
+// overlapped with the tree computation), and the host-side fault hook.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+
+#include "../../include/nrm.h"
+#include "nrm_device.cuh"
+#include "nrm_internal.h"
+
+using nrm::VecPlan;
+
+// --- host-side fault injection (tests only): the next `count` workspace
+// allocations report NRM_ENOMEM without calling cudaMalloc. -----------------
+static std::atomic<int> g_fail_alloc{0};
+
+extern "C" void nrm_test_inject_alloc_failures(int count) { g_fail_alloc.store(count < 0 ? 0 : count); }
+
+bool nrm_test_fail_alloc() {
+    int v = g_fail_alloc.load();
+    while (v > 0) {
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return true;
+    }
+    return false;
+}
+
+// --- graphs ---------------------------------------------------------------
+void nrm_graph_free(nrm_graph *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+extern "C" nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len,
+                                      const int64_t *offsets, int64_t B, double p, void *out, int32_t *status,
+                                      nrm_graph **graph) {
+    if (!ctx || !graph) return NRM_EINVAL;
+    *graph = nullptr;
+    if (B <= 0 || !offsets || !out || x_len < 0 || (x_len > 0 && !x) || !(p > 0.0) ||
+        (dtype != NRM_F32 && dtype != NRM_F64))
+        return NRM_EINVAL;
+    nrm_status st = nrm_ctx_ensure(ctx, nrm_batch_ws_bytes(ctx, dtype, x_len, B));
+    if (st != NRM_OK) return st;
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        ctx->err = cudaGetErrorString(e);
+        return NRM_ECUDA;
+    }
+    nrm_graph *g = new nrm_graph{ctx, nullptr, nullptr};
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = nrm_batch_impl(ctx, dtype, x, x_len, offsets, B, p, out, status, s);
+        cudaError_t e2 = cudaStreamEndCapture(s, &g->graph);
+        if (st == NRM_OK && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && st == NRM_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    cudaStreamDestroy(s);
+    if (st != NRM_OK || e != cudaSuccess) {
+        if (e != cudaSuccess) ctx->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        nrm_graph_free(g);
+        return st != NRM_OK ? st : NRM_ECUDA;
+    }
+    ctx->graphs.push_back(g);
+    *graph = g;
+    return NRM_OK;
+}
+
+extern "C" nrm_status nrm_graph_launch(nrm_graph *graph, void *stream) {
+    if (!graph || !graph->exec) return NRM_EINVAL;
+    cudaError_t e = cudaGraphLaunch(graph->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        graph->ctx->err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+        return NRM_ECUDA;
+    }
+    graph->ctx->launches += 2;
+    return NRM_OK;
+}
+
+extern "C" nrm_status nrm_graph_destroy(nrm_graph *graph) {
+    if (!graph) return NRM_OK;
+    nrm_ctx *c = graph->ctx;
+    auto it = std::find(c->graphs.begin(), c->graphs.end(), graph);
+    if (it != c->graphs.end()) c->graphs.erase(it);
+    nrm_graph_free(graph);
+    return NRM_OK;
+}
+
+// --- end-to-end call on host buffers -----------------------------------------
+void nrm_host_free(nrm_ctx *c) {
+    if (c->stage) cudaFree(c->stage);
+    if (c->out_dev) cudaFree(c->out_dev);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    if (c->s_copy) cudaStreamDestroy(c->s_copy);
+    if (c->s_comp) cudaStreamDestroy(c->s_comp);
+    c->stage = nullptr;
+    c->out_dev = nullptr;
+    c->s_copy = c->s_comp = nullptr;
+    c->stage_bytes = 0;
+}
+
+// first row of work item i at depth dw of the row tree over m rows (the same
+// root-to-node walk the kernel does)
+static int64_t host_node_start(int64_t m, uint32_t j, int d) {
+    int64_t start = 0, size = m;
+    for (int l = d - 1; l >= 0; --l) {
+        const int64_t left = (size + 1) >> 1;
+        if ((j >> l) & 1u) {
+            start += left;
+            size -= left;
+        } else {
+            size = left;
+        }
+    }
+    return start;
+}
+
+static const int kChunks = 8;
+
+extern "C" nrm_status nrm_host(nrm_ctx *ctx, nrm_dtype dtype, const void *x_host, int64_t n, double p,
+                               void *out_host) {
+    if (!ctx || !out_host || n < 0 || (n > 0 && !x_host) || (dtype != NRM_F32 && dtype != NRM_F64))
+        return NRM_EINVAL;
+    if (!(p > 0.0) || (dtype == NRM_F32 && !((float)p > 0.0f))) return NRM_EINVAL;
+    const size_t es = dtype == NRM_F64 ? 8 : 4;
+    const int P = dtype == NRM_F64 ? 64 : 128;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return NRM_ECUDA;
+    if (!ctx->s_copy) {
+        cudaStreamCreateWithFlags(&ctx->s_copy, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking);
+        ctx->ev.resize(kChunks);
+        for (auto &ev : ctx->ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (cudaMalloc(&ctx->out_dev, 16) != cudaSuccess) {
+            cudaGetLastError();
+            return NRM_ENOMEM;
+        }
+    }
+    if (n == 0) {
+        memset(out_host, 0, es);
+        return NRM_OK;
+    }
+    const size_t need = (size_t)n * es;
+    if (need > ctx->stage_bytes) {
+        if (ctx->stage) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+        }
+        if (nrm_test_fail_alloc()) return NRM_ENOMEM;
+        e = cudaMalloc(&ctx->stage, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->err = "cudaMalloc(stage): " + std::string(cudaGetErrorString(e));
+            return NRM_ENOMEM;
+        }
+        ctx->stage_bytes = need;
+    }
+    VecPlan pl;
+    nrm_status st = nrm_plan_single(ctx, dtype, n, &pl);
+    if (st != NRM_OK) return st;
+    // make sure the workspace exists before queueing anything
+    st = nrm_ctx_ensure(ctx, nrm_workspace_bytes(ctx, dtype, n, 1));
+    if (st != NRM_OK) return st;
+    const int64_t items = int64_t(1) << pl.dw;
+    const int64_t chunks = std::min<int64_t>(kChunks, items);
+    for (int64_t c = 0; c < chunks; ++c) {
+        const int64_t i0 = items * c / chunks, i1 = items * (c + 1) / chunks;
+        const int64_t r0 = host_node_start(pl.m, (uint32_t)i0, pl.dw);
+        const int64_t r1 = (i1 == items) ? pl.m : host_node_start(pl.m, (uint32_t)i1, pl.dw);
+        const int64_t e0 = r0 * P, e1 = std::min<int64_t>(n, r1 * P);
+        e = cudaMemcpyAsync((char *)ctx->stage + e0 * es, (const char *)x_host + e0 * es, (size_t)(e1 - e0) * es,
+                            cudaMemcpyHostToDevice, ctx->s_copy);
+        if (e != cudaSuccess) break;
+        cudaEventRecord(ctx->ev[c], ctx->s_copy);
+        cudaStreamWaitEvent(ctx->s_comp, ctx->ev[c], 0);
+        st = nrm_run_single_range(ctx, dtype, ctx->stage, n, p, ctx->out_dev, ctx->s_comp, &pl, i0, i1);
+        if (st != NRM_OK) break;
+    }
+    if (e == cudaSuccess && st == NRM_OK)
+        e = cudaMemcpyAsync(out_host, ctx->out_dev, es, cudaMemcpyDeviceToHost, ctx->s_comp);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->s_comp);
+    cudaStreamSynchronize(ctx->s_copy);
+    if (st != NRM_OK) return st;
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        ctx->err = std::string("nrm_host: ") + cudaGetErrorString(e);
+        return NRM_ECUDA;
+    }
+    return NRM_OK;
+}

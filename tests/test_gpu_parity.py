@@ -1,0 +1,458 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Bitwise for every result (the tree and every rounding are fixed), NaN-ness
+for NaN results; accuracy against the binary128 reference with the stated
+tolerances (1e-14 for binary64, 5e-6 for binary32) and the Eq. ubr bound.
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_06220_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+EPS_D, EPS_S = 2.0 ** -53, 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def nrm():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_06220_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+DEV = "cuda:0"
+TD = {np.float64: torch.float64, np.float32: torch.float32}
+
+
+def bits_equal(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if a.dtype != b.dtype or a.shape != b.shape:
+        return False
+    an, bn = np.isnan(a), np.isnan(b)
+    if (an != bn).any():
+        return False
+    return a[~an].tobytes() == b[~bn].tobytes()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def gpu_norms(nrm, x_dev, ns, p=2.0, starts=None):
+    """Norms of x_dev[s:s+n] for the given (start, n) list, one call each,
+    results gathered on the device and copied back once."""
+    out = torch.empty(len(ns), dtype=x_dev.dtype, device=DEV)
+    for i, n in enumerate(ns):
+        s = 0 if starts is None else starts[i]
+        nrm.nrmp(x_dev[s:s + n], p, out=out[i])
+    return out.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_device_generator_matches_host(nrm, dt):
+    for seed, vec, emin, emax, start in ((0, 0, -20, 20, 0), (3, 7, -8, 8, 12345), (1, 2, 125, 125, 0),
+                                         (9, 1, -126, -120, 5)):
+        if dt == np.float64 and emin == 125:
+            emin = emax = 1020
+        n = (1 << 18) + 13
+        h = inputs.vector(n, seed, vec, dt, emin, emax, start=start)
+        d = nrm.nrm_gen(n, seed, vec, TD[dt], emin, emax, start=start, device=DEV).cpu().numpy()
+        assert h.tobytes() == d.tobytes()
+    x, off = inputs.ragged_batch(50, seed=4, dtype=dt, max_log2=10)
+    d = nrm.nrm_gen_ragged(dev(off), seed=4, dtype=TD[dt]).cpu().numpy()
+    assert x.tobytes() == d.tobytes()
+
+
+# ---------------------------------------------------------------------------
+# single vectors
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_all_small_n(nrm, dt):
+    """Every n up to 40 rows (several groups, items and a ragged tail)."""
+    P = 64 if dt == np.float64 else 128
+    ns = list(range(0, 40 * P + 2))
+    x = inputs.vector(max(ns), seed=1, vec=3, dtype=dt)
+    got = gpu_norms(nrm, dev(x), ns)
+    want = np.array([oracle.nrm(x[:n]) for n in ns], dtype=dt)
+    bad = [n for n, g, w in zip(ns, got, want) if not bits_equal(g, w)]
+    assert not bad, bad[:10]
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_misaligned_starts(nrm, dt):
+    """Z^u == Z^a (Section 3): any element offset gives the same bits as a
+    copy at an aligned address."""
+    x = inputs.vector(300000, seed=2, vec=3, dtype=dt)
+    xd = dev(x)
+    ns, starts = [], []
+    r = random.Random(3)
+    for s in range(0, 9):
+        for n in (1, 5, 63, 64, 65, 127, 128, 129, 1000, 4097, r.randint(1, 250000)):
+            ns.append(n)
+            starts.append(s)
+    got = gpu_norms(nrm, xd, ns, starts=starts)
+    for g, n, s in zip(got, ns, starts):
+        assert bits_equal(g, oracle.nrm(x[s:s + n])), (n, s)
+        aligned = dev(x[s:s + n].copy())
+        assert bits_equal(g, nrm.nrmf(aligned).item() if dt == np.float64 else np.float32(nrm.nrmf(aligned).item()))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_sizes_primes_powers(nrm, dt):
+    ns = []
+    for k in range(1, 23):
+        ns += [(1 << k) - 1, 1 << k, (1 << k) + 1]
+    ns += [1009, 65537, 999983, 1299709, 3 * (1 << 20) + 7]
+    x = inputs.vector(max(ns), seed=3, vec=0, dtype=dt)
+    got = gpu_norms(nrm, dev(x), ns)
+    for g, n in zip(got, ns):
+        assert bits_equal(g, oracle.nrm(x[:n])), n
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("p", [1.0, 1.5, 3.0, 7.5, 0.5, 2.0 / 3.0, math.inf, math.pi])
+def test_pnorm_parity(nrm, dt, p):
+    ns = [1, 2, 63, 64, 65, 129, 1000, 8191, 65536, 100003]
+    x = inputs.vector(max(ns), seed=4, vec=1, dtype=dt, emin=-8, emax=8)
+    got = gpu_norms(nrm, dev(x), ns, p=p)
+    for g, n in zip(got, ns):
+        assert bits_equal(g, oracle.nrm(x[:n], p)), (n, p)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_tuning_invariance(nrm, dt):
+    """No tuning knob changes a bit (the tree is fixed by P alone)."""
+    ns = [1, 100, 5000, 123457, 1 << 20, (1 << 21) + 3]
+    x = inputs.vector(max(ns), seed=5, vec=0, dtype=dt)
+    xd = dev(x)
+    want = np.array([oracle.nrm(x[:n]) for n in ns], dtype=dt)
+    ctx = nrm.Context(0)
+    try:
+        for g in (2, 3):
+            for wpb in (4, 8, 16):
+                for k in (g, g + 2, g + 4, g + 10):
+                    for bps in (1, 4):
+                        ctx.set_tuning(g, wpb, k, bps)
+                        out = torch.empty(len(ns), dtype=xd.dtype, device=DEV)
+                        for i, n in enumerate(ns):
+                            nrm.nrmp(xd[:n], 2.0, out=out[i], ctx=ctx)
+                        assert bits_equal(out.cpu().numpy(), want), (g, wpb, k, bps)
+    finally:
+        ctx.close()
+
+
+def test_repeat_stability(nrm):
+    """200 launches of the same call give the same bits (a race would show)."""
+    x = dev(inputs.vector((1 << 22) + 77, seed=6, vec=0))
+    out = torch.empty(200, dtype=torch.float64, device=DEV)
+    for i in range(200):
+        nrm.nrmf(x, out=out[i])
+    o = out.cpu().numpy()
+    assert len(set(o.tobytes()[i * 8:(i + 1) * 8] for i in range(200))) == 1
+
+
+def test_config0_bitwise_and_accuracy(nrm):
+    """n = 2^20 binary64, e in [-20, 20], seed 0: bitwise and relerr."""
+    x = inputs.vector(1 << 20, seed=0, vec=0)
+    g = nrm.nrmf(dev(x)).item()
+    assert bits_equal(np.float64(g), oracle.nrm(x))
+    e = oracle.relerr(g, x, nthreads=8)
+    assert e <= 1e-14
+    hi, lo = oracle.ub_relerr(oracle.tree_depth(x.size, 64))
+    assert e <= (hi + lo) * EPS_D
+
+
+def test_special_values(nrm):
+    """Infinities give +inf; NaNs follow Listing 2 literally (NaN-ness
+    compared); subnormal inputs are kept (no flush to zero)."""
+    for dt in (np.float64, np.float32):
+        x = inputs.vector(10000, seed=7, vec=0, dtype=dt)
+        y = x.copy()
+        y[1234] = np.inf
+        assert math.isinf(nrm.nrmf(dev(y)).item())
+        for pos in (0, 1, 63, 64, 5000, 9999):
+            z = x.copy()
+            z[pos] = np.nan
+            for p in (2.0, 1.0, 3.0, math.inf):
+                assert bits_equal(np.asarray(nrm.nrmp(dev(z), p).item(), dtype=dt), oracle.nrm(z, p)), (pos, p)
+        tiny = np.finfo(dt).smallest_subnormal
+        s = (np.arange(1, 3001) % 7).astype(dt) * tiny
+        for p in (2.0, 1.0, 3.0):
+            assert bits_equal(np.asarray(nrm.nrmp(dev(s), p).item(), dtype=dt), oracle.nrm(s, p))
+
+
+def test_invalid_arguments(nrm):
+    import ctypes
+    L = nrm.load()
+    c = nrm.context(0)
+    vp = ctypes.c_void_p
+    o = torch.empty(4, dtype=torch.float64, device=DEV)
+    x = torch.ones(8, dtype=torch.float64, device=DEV)
+    assert L.nrmf_d(c.h, vp(x.data_ptr()), -1, vp(o.data_ptr()), None) == nrm.NRM_EINVAL
+    assert L.nrmf_d(c.h, vp(0), 5, vp(o.data_ptr()), None) == nrm.NRM_EINVAL
+    assert L.nrmf_d(c.h, vp(x.data_ptr()), 5, vp(0), None) == nrm.NRM_EINVAL
+    assert L.nrmp_d(c.h, vp(x.data_ptr()), 5, 0.0, vp(o.data_ptr()), None) == nrm.NRM_EINVAL
+    assert L.nrmp_d(c.h, vp(x.data_ptr()), 5, -2.0, vp(o.data_ptr()), None) == nrm.NRM_EINVAL
+    assert L.nrmp_d(c.h, vp(x.data_ptr()), 5, float("nan"), vp(o.data_ptr()), None) == nrm.NRM_EINVAL
+    assert L.nrm_batch(c.h, 5, vp(x.data_ptr()), 8, vp(0), 1, 2.0, vp(o.data_ptr()), vp(0), None) == nrm.NRM_EINVAL
+    # n == 0 gives +0
+    o.fill_(7.0)
+    assert L.nrmf_d(c.h, vp(0), 0, vp(o.data_ptr()), None) == nrm.NRM_OK
+    torch.cuda.synchronize()
+    assert o[0].item() == 0.0 and math.copysign(1, o[0].item()) > 0
+
+
+def test_alloc_failure_is_reported(nrm):
+    """Host-side fault injection: a failed workspace allocation returns
+    NRM_ENOMEM and leaves the context usable."""
+    L = nrm.load()
+    ctx = nrm.Context(0)
+    try:
+        x = dev(inputs.vector(1 << 24, seed=8, vec=0))
+        L.nrm_test_inject_alloc_failures(1)
+        with pytest.raises(nrm.NrmError) as ei:
+            nrm.nrmf(x, ctx=ctx)
+        assert ei.value.status == nrm.NRM_ENOMEM
+        L.nrm_test_inject_alloc_failures(0)
+        g = nrm.nrmf(x, ctx=ctx).item()
+        assert bits_equal(np.float64(g), oracle.nrm(x.cpu().numpy()))
+    finally:
+        L.nrm_test_inject_alloc_failures(0)
+        ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# full size (n = 2^28), probes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_full_size_2e28(nrm, dt):
+    """n = 2^28, seeds 1..3 (binary64 2 GiB / binary32 1 GiB): bitwise
+    against the oracle on seed 1 and relerr against binary128 within the
+    tolerance and the Eq. ubr bound on every seed."""
+    n = 1 << 28
+    P = 64 if dt == np.float64 else 128
+    tol = 1e-14 if dt == np.float64 else 5e-6
+    hi, lo = oracle.ub_relerr(oracle.tree_depth(n, P), "D" if dt == np.float64 else "S")
+    bound = (hi + lo) * (EPS_D if dt == np.float64 else EPS_S)
+    for seed in (1, 2, 3):
+        xd = nrm.nrm_gen(n, seed, 0, TD[dt], device=DEV)
+        g = nrm.nrmf(xd).item()
+        x = xd.cpu().numpy()
+        del xd
+        if seed == 1:
+            assert bits_equal(np.asarray(g, dtype=dt), oracle.nrm(x))
+        e = oracle.relerr(g, x, nthreads=16)
+        assert e <= tol and e <= bound, (seed, e)
+        del x
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_overflow_underflow_probes_full_size(nrm, dt):
+    """Probes at n = 2^28: (i) entries in [2^1020, 2^1021) (D) /
+    [2^125, 2^126) (S): the true norm exceeds the range, result +inf, no
+    NaN; (iii) data x 2^k for the largest k keeping the result finite is
+    exactly 2^k times the unscaled result; underflow: data x 2^-k with every
+    entry still normal is exactly 2^-k times the result."""
+    n = 1 << 28
+    big = 1020 if dt == np.float64 else 125
+    xd = nrm.nrm_gen(n, 2, 0, TD[dt], emin=big, emax=big, device=DEV)
+    g = nrm.nrmf(xd).item()
+    assert math.isinf(g) and g > 0
+    del xd
+    xd = nrm.nrm_gen(n, 3, 0, TD[dt], device=DEV)
+    v = nrm.nrmf(xd).item()
+    info = np.finfo(dt)
+    kmax = int(math.floor(math.log2(float(info.max)) - math.log2(v))) - 1
+    kmin = -int(info.minexp) - 20  # entries >= 2^-20 stay >= the smallest normal: 1002 (D), 106 (S)
+    scale_up = torch.tensor(2.0 ** kmax, dtype=TD[dt], device=DEV)
+    vu = nrm.nrmf(xd * scale_up).item()
+    assert np.asarray(vu, dtype=dt) == np.asarray(v, dtype=dt) * np.asarray(2.0 ** kmax, dtype=dt)
+    scale_dn = torch.tensor(2.0 ** (-kmin), dtype=TD[dt], device=DEV)
+    xs = xd * scale_dn
+    assert float(xs.abs().min()) >= float(info.tiny)
+    vd = nrm.nrmf(xs).item()
+    assert np.asarray(vd, dtype=dt) == np.asarray(v, dtype=dt) * np.asarray(2.0 ** (-kmin), dtype=dt)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_underflow_probe_smallest_normal(nrm, dt):
+    """All entries in [2^-1022, 2^-1021) (D) / [2^-126, 2^-125) (S): squares
+    underflow, the tree does not; bitwise against the oracle and accurate
+    against binary128."""
+    lo_e = -1022 if dt == np.float64 else -126
+    n = (1 << 22) + 5
+    xd = nrm.nrm_gen(n, 4, 0, TD[dt], emin=lo_e, emax=lo_e, device=DEV)
+    g = nrm.nrmf(xd).item()
+    x = xd.cpu().numpy()
+    assert bits_equal(np.asarray(g, dtype=dt), oracle.nrm(x))
+    hi, _ = oracle.ref_q128(x, nthreads=8)
+    assert abs(g - hi) / hi <= (1e-14 if dt == np.float64 else 5e-6)
+
+
+# ---------------------------------------------------------------------------
+# host buffers (end to end)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_nrm_host_matches_device(nrm, dt):
+    for n in (0, 1, 1000, (1 << 22) + 3):
+        x = inputs.vector(n, seed=9, vec=0, dtype=dt)
+        for p in (2.0, 3.0):
+            h = nrm.nrm_host(x, p)
+            assert bits_equal(np.asarray(h, dtype=dt), oracle.nrm(x, p) if n else dt(0)), (n, p)
+    xp = torch.from_numpy(inputs.vector(1 << 20, seed=9, vec=1, dtype=dt)).pin_memory()
+    assert bits_equal(np.asarray(nrm.nrm_host(xp), dtype=dt), oracle.nrm(xp.numpy()))
+
+
+# ---------------------------------------------------------------------------
+# ragged batches
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("p", [2.0, 1.0, 3.0])
+def test_batch_matches_oracle(nrm, dt, p):
+    x, off = inputs.ragged_batch(700, seed=10, dtype=dt, max_log2=16)
+    out, st = nrm.nrm_batch(dev(x), dev(off), p)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    assert bits_equal(out.cpu().numpy(), oracle.nrm_batch(x, off, p))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_batch_config2_sampled(nrm, dt):
+    """4096 vectors, lengths log-uniform in [1, 2^18] (about 86 M elements),
+    generated on the device; 200 sampled vectors against the oracle, and the
+    whole batch equal to one call per vector."""
+    L = inputs.ragged_lengths(4096, seed=0)
+    off = np.zeros(4097, np.int64)
+    np.cumsum(L, out=off[1:])
+    offd = dev(off)
+    xd = nrm.nrm_gen_ragged(offd, seed=0, dtype=TD[dt])
+    out, st = nrm.nrm_batch(xd, offd)
+    single = torch.empty(4096, dtype=TD[dt], device=DEV)
+    for i in range(4096):
+        nrm.nrmf(xd[off[i]:off[i + 1]], out=single[i])
+    o = out.cpu().numpy()
+    assert (st.cpu().numpy() == 0).all()
+    assert bits_equal(o, single.cpu().numpy())
+    x = xd.cpu().numpy()
+    for i in random.Random(1).sample(range(4096), 200):
+        assert bits_equal(o[i], oracle.nrm(x[off[i]:off[i + 1]])), i
+
+
+def test_batch_bad_offsets(nrm):
+    x = inputs.vector(1000, seed=11, vec=0)
+    off = np.array([0, 10, 5, 300, 300, 1200, 1000, -3, 1000], np.int64)
+    out, st = nrm.nrm_batch(dev(x), dev(off))
+    o, s = out.cpu().numpy(), st.cpu().numpy()
+    want_ok = {0: (0, 10), 2: (5, 300), 3: (300, 300)}
+    for i in range(len(off) - 1):
+        if i in want_ok:
+            a, b = want_ok[i]
+            assert s[i] == 0
+            assert bits_equal(o[i], oracle.nrm(x[a:b]))
+        else:
+            assert s[i] == nrm.NRM_EINVAL and math.isnan(o[i]), i
+
+
+def test_batch_overlap_guard(nrm):
+    """Overlapping offsets that would need more workspace than x_len
+    implies: every vector reports NRM_ENOMEM, nothing is computed."""
+    x = inputs.vector(1 << 16, seed=12, vec=0)
+    n = x.size
+    off = np.array([0, n, 0, n, 0, n, 0, n, 0, n], np.int64)
+    out, st = nrm.nrm_batch(dev(x), dev(off))
+    s = st.cpu().numpy()
+    assert set(s[::2].tolist()) <= {0, nrm.NRM_ENOMEM}
+    ok = s == 0
+    o = out.cpu().numpy()
+    for i in np.nonzero(ok)[0]:
+        a, b = off[i], off[i + 1]
+        assert bits_equal(o[i], oracle.nrm(x[a:b]))
+
+
+def test_batch_graph_replay(nrm):
+    x, off = inputs.ragged_batch(300, seed=13, max_log2=15)
+    xd, offd = dev(x), dev(off)
+    g = nrm.nrm_batch_graph(xd, offd)
+    out, st = g.launch()
+    torch.cuda.synchronize()
+    assert bits_equal(out.cpu().numpy(), oracle.nrm_batch(x, off))
+    # new data in the same buffers: the replay recomputes
+    nrm.nrm_gen_ragged(offd, seed=14, out=xd)
+    out2, _ = g.launch()
+    torch.cuda.synchronize()
+    assert bits_equal(out2.cpu().numpy(), oracle.nrm_batch(xd.cpu().numpy(), off))
+    g.close()
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_batch_tuning_and_composition_invariance(nrm, dt):
+    """A vector's norm does not depend on the batch it is in, nor on tuning."""
+    x, off = inputs.ragged_batch(200, seed=15, dtype=dt, max_log2=17)
+    want = oracle.nrm_batch(x, off)
+    xd = dev(x)
+    ctx = nrm.Context(0)
+    try:
+        for g, wpb, k in ((2, 4, 2), (3, 8, 7), (3, 16, 5), (2, 8, 12)):
+            ctx.set_tuning(g, wpb, k, 4)
+            out, _ = nrm.nrm_batch(xd, dev(off), ctx=ctx)
+            assert bits_equal(out.cpu().numpy(), want), (g, wpb, k)
+        # subsets and a reversed order
+        idx = list(range(0, 200, 3))[::-1]
+        sub_off = [0]
+        parts = []
+        for i in idx:
+            parts.append(x[off[i]:off[i + 1]])
+            sub_off.append(sub_off[-1] + off[i + 1] - off[i])
+        xs = np.concatenate(parts)
+        out, _ = nrm.nrm_batch(dev(xs), dev(np.array(sub_off, np.int64)), ctx=ctx)
+        assert bits_equal(out.cpu().numpy(), want[idx])
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_config3_pnorm_batch(nrm, dt):
+    """1024 vectors of 2^16, e in [-8, 8], p in {1, 1.5, 3, 7.5}: 48 sampled
+    vectors bitwise against the oracle; constant vectors c repeated 2^16
+    times within tolerance of |c| 2^(16/p) (and exactly 2^16 |c| for p = 1)."""
+    B, n = 1024, 1 << 16
+    off = np.arange(B + 1, dtype=np.int64) * n
+    offd = dev(off)
+    xd = nrm.nrm_gen_ragged(offd, seed=16, dtype=TD[dt], emin=-8, emax=8)
+    x = xd.cpu().numpy()
+    tol = 1e-14 if dt == np.float64 else 5e-6
+    for p in (1.0, 1.5, 3.0, 7.5):
+        out, st = nrm.nrm_batch(xd, offd, p)
+        o = out.cpu().numpy()
+        for i in random.Random(int(p * 10)).sample(range(B), 12):
+            v = x[off[i]:off[i + 1]]
+            assert bits_equal(o[i], oracle.nrm(v, p)), (p, i)
+            assert oracle.relerr(o[i], v, p, nthreads=8) <= tol
+    for c in (1.0, -1.75, 3.0e-3):
+        cv = torch.full((B * n,), c, dtype=TD[dt], device=DEV)
+        for p in (1.0, 1.5, 3.0, 7.5):
+            out, _ = nrm.nrm_batch(cv, offd, p)
+            o = out.cpu().numpy().astype(np.float64)
+            cc = abs(float(dt(c)))
+            exact = cc * 2.0 ** (16.0 / float(dt(p)))
+            if p == 1.0:
+                assert (o == cc * n).all()
+            assert np.all(np.abs(o - exact) / exact <= tol), (c, p)
