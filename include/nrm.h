@@ -201,6 +201,10 @@ uint64_t nrm_kernel_launches(const nrm_ctx *ctx);
  * without calling cudaMalloc.  count <= 0 disarms it. */
 void nrm_test_inject_alloc_failures(int count);
 
+/* Test hook: copy the first `count` ticket counters of the context's
+ * workspace to host memory (synchronous).  Between calls they are all zero. */
+nrm_status nrm_test_read_tickets(const nrm_ctx *ctx, uint32_t *host, int64_t count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,7 @@ def load():
         "nrm_gen_ragged": (st, [i32, vp, i64, vp, i64, u64, i32, i32, vp]),
         "nrm_kernel_launches": (u64, [vp]),
         "nrm_test_inject_alloc_failures": (None, [ctypes.c_int]),
+        "nrm_test_read_tickets": (st, [vp, vp, i64]),
     }
     for name, (res, args) in sigs.items():
         if hasattr(L, name):

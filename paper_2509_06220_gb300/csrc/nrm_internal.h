@@ -23,8 +23,10 @@ struct nrm_graph {
 struct nrm_ctx {
     int device = 0;
     int sms = 1;
-    void *ws = nullptr;
+    void *ws = nullptr;        // partial-norm slots, batch plans, totals, cursor
     size_t ws_bytes = 0;
+    unsigned *tickets = nullptr; // one counter per internal tree node; all zero between calls
+    int64_t tickets_cap = 0;
     nrm_tuning tune{};
     std::string err;
     uint64_t launches = 0;
@@ -37,13 +39,14 @@ struct nrm_ctx {
     void *out_dev = nullptr;
 };
 
-nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes);
+nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes, int64_t tickets = 0);
 nrm_status nrm_plan_single(const nrm_ctx *c, nrm_dtype dt, int64_t n, nrm::VecPlan *pl);
 nrm_status nrm_run_single_range(nrm_ctx *c, nrm_dtype dt, const void *x, int64_t n, double p, void *out,
                                 cudaStream_t s, const nrm::VecPlan *pl, int64_t item_lo, int64_t item_hi);
 nrm_status nrm_batch_impl(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
                           int64_t B, double p, void *out, int32_t *status, cudaStream_t s);
 size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);
+int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);
 void nrm_graph_free(nrm_graph *g);
 void nrm_host_free(nrm_ctx *c);
 bool nrm_test_fail_alloc();

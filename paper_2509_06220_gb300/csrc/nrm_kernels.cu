@@ -282,17 +282,18 @@ constexpr int DW_MAX = 20;
 
 template <typename T> constexpr int P_of() { return Geo<T>::P; }
 
+// Workspace layout of one call (the tickets live in their own buffer, see
+// nrm_ctx::tickets, so that no other data ever occupies a ticket).
 struct Layout {
-    size_t tickets, slots, plans, totals, cursor, end;
+    size_t slots, plans, totals, cursor, end;
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 static Layout layout_for(int64_t nodes, int64_t B) {
     Layout L;
-    L.tickets = 0;
-    L.slots = align256(sizeof(unsigned) * (size_t)std::max<int64_t>(nodes, 1));
-    L.plans = L.slots + align256(512 * (size_t)std::max<int64_t>(2 * nodes, 1));
+    L.slots = 0;
+    L.plans = align256(512 * (size_t)std::max<int64_t>(2 * nodes, 1));
     L.totals = L.plans + align256(sizeof(VecPlan) * (size_t)std::max<int64_t>(B, 1));
     L.cursor = L.totals + 256;
     L.end = L.cursor + 256;
@@ -314,30 +315,47 @@ static nrm_status set_cuda_err(nrm_ctx *c, cudaError_t e, const char *where) {
     return NRM_ECUDA;
 }
 
-nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes) {
-    if (bytes <= c->ws_bytes) return NRM_OK;
+// Grow the workspace to `bytes` and the ticket array to `tickets` counters.
+// Tickets are zeroed when allocated and are returned to zero by every call
+// (each node's second arriver resets its ticket), so they never need
+// clearing between calls.
+nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes, int64_t tickets) {
+    if (bytes <= c->ws_bytes && tickets <= c->tickets_cap) return NRM_OK;
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return set_cuda_err(c, e, "cudaSetDevice");
-    if (c->ws) {
-        e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return set_cuda_err(c, e, "cudaDeviceSynchronize");
-        cudaFree(c->ws);
+    e = cudaDeviceSynchronize(); // the old buffers may still be in use
+    if (e != cudaSuccess) return set_cuda_err(c, e, "cudaDeviceSynchronize");
+    if (bytes > c->ws_bytes) {
+        if (c->ws) cudaFree(c->ws);
         c->ws = nullptr;
         c->ws_bytes = 0;
+        size_t want = std::max(bytes, (size_t)1 << 20);
+        if (nrm_test_fail_alloc()) return NRM_ENOMEM;
+        e = cudaMalloc(&c->ws, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->ws = nullptr;
+            return set_cuda_err(c, e, "cudaMalloc(workspace)");
+        }
+        c->ws_bytes = want;
     }
-    size_t want = std::max(bytes, (size_t)1 << 20);
-    if (nrm_test_fail_alloc()) return NRM_ENOMEM;
-    e = cudaMalloc(&c->ws, want);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        c->ws = nullptr;
-        return set_cuda_err(c, e, "cudaMalloc(workspace)");
+    if (tickets > c->tickets_cap) {
+        if (c->tickets) cudaFree(c->tickets);
+        c->tickets = nullptr;
+        c->tickets_cap = 0;
+        int64_t want = std::max<int64_t>(tickets, 1 << 16);
+        if (nrm_test_fail_alloc()) return NRM_ENOMEM;
+        e = cudaMalloc(&c->tickets, (size_t)want * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->tickets = nullptr;
+            return set_cuda_err(c, e, "cudaMalloc(tickets)");
+        }
+        e = cudaMemset(c->tickets, 0, (size_t)want * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return set_cuda_err(c, e, "cudaMemset(tickets)");
+        c->tickets_cap = want;
     }
-    e = cudaMemset(c->ws, 0, want); // tickets start at zero
-    if (e != cudaSuccess) return set_cuda_err(c, e, "cudaMemset(workspace)");
-    e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return set_cuda_err(c, e, "cudaDeviceSynchronize");
-    c->ws_bytes = want;
     return NRM_OK;
 }
 
@@ -359,7 +377,7 @@ extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
     cudaGetDeviceProperties(&prop, device);
     c->sms = prop.multiProcessorCount;
     c->tune = nrm_tuning{3, 8, 7, 4};
-    nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20);
+    nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20, 1 << 16);
     if (s != NRM_OK) {
         delete c;
         return s;
@@ -376,6 +394,7 @@ extern "C" nrm_status nrm_destroy(nrm_ctx *ctx) {
     ctx->graphs.clear();
     nrm_host_free(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->tickets) cudaFree(ctx->tickets);
     delete ctx;
     return NRM_OK;
 }
@@ -397,7 +416,8 @@ extern "C" const char *nrm_last_error(const nrm_ctx *ctx) { return ctx ? ctx->er
 
 extern "C" nrm_status nrm_reserve(nrm_ctx *ctx, size_t bytes) {
     if (!ctx) return NRM_EINVAL;
-    return nrm_ctx_ensure(ctx, bytes);
+    // slots need 1 KiB per ticket node: reserve tickets for what fits
+    return nrm_ctx_ensure(ctx, bytes, (int64_t)(bytes / 1024) + 1);
 }
 
 extern "C" nrm_status nrm_get_tuning(const nrm_ctx *ctx, nrm_tuning *t) {
@@ -417,6 +437,12 @@ extern "C" nrm_status nrm_set_tuning(nrm_ctx *ctx, const nrm_tuning *t) {
 }
 
 extern "C" uint64_t nrm_kernel_launches(const nrm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" nrm_status nrm_test_read_tickets(const nrm_ctx *ctx, uint32_t *host, int64_t count) {
+    if (!ctx || !host || count < 0 || count > ctx->tickets_cap) return NRM_EINVAL;
+    cudaError_t e = cudaMemcpy(host, ctx->tickets, (size_t)count * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
 
 // single-vector planning ------------------------------------------------------
 
@@ -491,7 +517,7 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
     const int64_t items = int64_t(1) << pl.dw;
     const int64_t nodes = items - 1;
     Layout L = layout_for(nodes, 1);
-    nrm_status st = nrm_ctx_ensure(c, L.end);
+    nrm_status st = nrm_ctx_ensure(c, L.end, nodes);
     if (st != NRM_OK) return st;
     TreeArgs<T> a{};
     a.x = x;
@@ -503,7 +529,7 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
     a.item_hi = plan_in ? item_hi : items;
     a.total_items = nullptr;
     a.cursor = nullptr;
-    a.tickets = reinterpret_cast<unsigned *>((char *)c->ws + L.tickets);
+    a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>((char *)c->ws + L.slots);
     const int64_t warps = a.item_hi - a.item_lo;
     cudaError_t e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, warps, s); });
@@ -557,6 +583,10 @@ static int64_t batch_nodes_bound(const nrm_ctx *c, int64_t x_len, int64_t B, int
     return (2 * rows >> k) + 2;
 }
 
+int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B) {
+    return batch_nodes_bound(c, x_len, B, dt == NRM_F64 ? 64 : 128);
+}
+
 size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B) {
     const int P = dt == NRM_F64 ? 64 : 128;
     return layout_for(batch_nodes_bound(c, x_len, B, P), B).end;
@@ -578,7 +608,7 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     constexpr int P = Geo<T>::P;
     const int64_t nodes_bound = batch_nodes_bound(c, x_len, B, P);
     Layout L = layout_for(nodes_bound, B);
-    nrm_status st = nrm_ctx_ensure(c, L.end);
+    nrm_status st = nrm_ctx_ensure(c, L.end, nodes_bound);
     if (st != NRM_OK) return st;
     char *ws = (char *)c->ws;
     VecPlan *plans = reinterpret_cast<VecPlan *>(ws + L.plans);
@@ -596,7 +626,7 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     a.B = B;
     a.total_items = totals;
     a.cursor = cursor;
-    a.tickets = reinterpret_cast<unsigned *>(ws + L.tickets);
+    a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>(ws + L.slots);
     const int64_t persistent = (int64_t)c->sms * 64 * c->tune.warps_per_block; // capped by occupancy
     e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, persistent, s); });

@@ -43,7 +43,7 @@ extern "C" nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void 
     if (B <= 0 || !offsets || !out || x_len < 0 || (x_len > 0 && !x) || !(p > 0.0) ||
         (dtype != NRM_F32 && dtype != NRM_F64))
         return NRM_EINVAL;
-    nrm_status st = nrm_ctx_ensure(ctx, nrm_batch_ws_bytes(ctx, dtype, x_len, B));
+    nrm_status st = nrm_ctx_ensure(ctx, nrm_batch_ws_bytes(ctx, dtype, x_len, B), nrm_batch_tickets(ctx, dtype, x_len, B));
     if (st != NRM_OK) return st;
     cudaStream_t s;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -166,7 +166,7 @@ extern "C" nrm_status nrm_host(nrm_ctx *ctx, nrm_dtype dtype, const void *x_host
     nrm_status st = nrm_plan_single(ctx, dtype, n, &pl);
     if (st != NRM_OK) return st;
     // make sure the workspace exists before queueing anything
-    st = nrm_ctx_ensure(ctx, nrm_workspace_bytes(ctx, dtype, n, 1));
+    st = nrm_ctx_ensure(ctx, nrm_workspace_bytes(ctx, dtype, n, 1), (int64_t(1) << pl.dw));
     if (st != NRM_OK) return st;
     const int64_t items = int64_t(1) << pl.dw;
     const int64_t chunks = std::min<int64_t>(kChunks, items);

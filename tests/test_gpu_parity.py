@@ -222,7 +222,9 @@ def test_alloc_failure_is_reported(nrm):
     L = nrm.load()
     ctx = nrm.Context(0)
     try:
-        x = dev(inputs.vector(1 << 24, seed=8, vec=0))
+        # 2^26 elements need more workspace than a fresh context holds
+        x = nrm.nrm_gen(1 << 26, 8, 0, torch.float64, device=DEV)
+        assert ctx.workspace_bytes(nrm.NRM_F64, x.numel()) > (4 << 20)
         L.nrm_test_inject_alloc_failures(1)
         with pytest.raises(nrm.NrmError) as ei:
             nrm.nrmf(x, ctx=ctx)
@@ -456,3 +458,24 @@ def test_config3_pnorm_batch(nrm, dt):
             if p == 1.0:
                 assert (o == cc * n).all()
             assert np.all(np.abs(o - exact) / exact <= tol), (c, p)
+
+
+def test_tickets_return_to_zero(nrm):
+    """Every call leaves all node tickets at zero (each node's second
+    arriver resets its ticket), across calls of different tree shapes and
+    batches -- the invariant the next call's combine relies on."""
+    import ctypes
+    L = nrm.load()
+    ctx = nrm.Context(0)
+    try:
+        x = dev(inputs.vector(1 << 21, seed=17, vec=0))
+        for n in (1000, 4097, 62381, 1 << 21, 3, 200000, 64):
+            nrm.nrmf(x[:n], ctx=ctx)
+        xb, off = inputs.ragged_batch(300, seed=18, max_log2=16)
+        nrm.nrm_batch(dev(xb), dev(off), ctx=ctx)
+        torch.cuda.synchronize()
+        t = np.zeros(1 << 16, np.uint32)
+        assert L.nrm_test_read_tickets(ctx.h, ctypes.c_void_p(t.ctypes.data), t.size) == 0
+        assert not t.any(), np.nonzero(t)[0][:20]
+    finally:
+        ctx.close()
