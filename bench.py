@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark: DNRMF and SNRMF on single vectors of n = 2^28 elements.
+
+One step is one pass of the hot path over one batch of synthetic input:
+xNRMF of a binary64 vector of 2^28 elements (2 GiB) followed by xNRMF of a
+binary32 vector of 2^28 elements (1 GiB), both resident in HBM (together 24x
+the L2, so no flush is needed between steps).  The metric is GB/s of input
+consumed per second of device time.
+
+Printed as one JSON line (rank 0):
+  value      whole-job GB/s (all ranks) with inputs already in HBM;
+  e2e        the same metric through the C ABI's host-buffer entry point
+             (nrm_host: pinned host input, chunked H2D copies overlapped with
+             the tree, result read back), copies inside the timed region;
+  roofline   for the dominant kernel (the binary64 tree kernel): its
+             algorithmic work per launch over its CUDA-event launch time,
+             against the measured or unit-count peak;
+  cpu_baseline  the C oracle on the same step, single-threaded;
+  parts      per-precision figures and the ragged-batch workload (4096
+             vectors, log-uniform lengths in [1, 2^18]) as graph replays
+             versus one launch per vector.
+Multi-GPU (torchrun): every rank computes its own pair of vectors (seed
+1 + rank); there is no data-path collective ("weak" scaling).
+--impl reference times the oracle (the reference arm for this build) on a
+bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1 << 28
+BYTES_D = N * 8
+BYTES_S = N * 4
+METRIC = "DNRMF+SNRMF GB/s at n=2^28 (FP64 2 GiB + FP32 1 GiB per step)"
+WORKLOAD = ("xNRMF of one FP64 and one FP32 vector of n=2^28 each, x_i = s*m*2^e, s=+-1, m uniform in [1,2), "
+            "e uniform in [-20,20], seed 1 (+rank)")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + SMI_FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [t.strip() for t in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        top = max(sm)
+        loaded = [v for v in sm if v >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def run_reference(args):
+    """The oracle (plain serial C) on a bounded sample of the workload:
+    each step computes xNRMF of the first 2^25 elements of the FP64 and of
+    the FP32 vector (the same generator), single-threaded."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2509_06220_gb300 import inputs
+    ns = 1 << 25
+    xd = inputs.vector(ns, seed=1, vec=0, dtype=np.float64)
+    xs = inputs.vector(ns, seed=1, vec=0, dtype=np.float32)
+    for _ in range(args.warmup):
+        oracle.nrm(xd)
+        oracle.nrm(xs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.nrm(xd)
+        oracle.nrm(xs)
+    dt = time.perf_counter() - t0
+    gbs = args.steps * ns * 12 / dt / 1e9
+    sample = "first 2^25 elements of each vector per step (FP64 + FP32), oracle single-threaded"
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "sample_n": ns},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_batch(nrm, torch, ctx, dev):
+    """Ragged batch of 4096 FP64 vectors, lengths log-uniform in [1, 2^18]:
+    graph replay of the persistent launch versus one launch per vector."""
+    import numpy as np
+
+    from paper_2509_06220_gb300 import inputs
+    L = inputs.ragged_lengths(4096, seed=0)
+    off = np.zeros(4097, np.int64)
+    np.cumsum(L, out=off[1:])
+    offd = torch.from_numpy(off).to(dev)
+    out = {}
+    for name, td in (("f64", torch.float64), ("f32", torch.float32)):
+        x = nrm.nrm_gen_ragged(offd, seed=0, dtype=td)
+        g = nrm.nrm_batch_graph(x, offd, ctx=ctx)
+        for _ in range(3):
+            g.launch()
+        torch.cuda.synchronize()
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        t_graph = e0.elapsed_time(e1) / reps
+        single = torch.empty(4096, dtype=td, device=dev)
+        views = [x[off[i]:off[i + 1]] for i in range(4096)]
+        for i in range(4096):
+            nrm.nrmf(views[i], out=single[i], ctx=ctx)
+        torch.cuda.synchronize()
+        e0.record()
+        for i in range(4096):
+            nrm.nrmf(views[i], out=single[i], ctx=ctx)
+        e1.record()
+        torch.cuda.synchronize()
+        t_single = e0.elapsed_time(e1)
+        same = bool(torch.equal(single.view(torch.int64 if td == torch.float64 else torch.int32),
+                                g.out.view(torch.int64 if td == torch.float64 else torch.int32)))
+        out["batch_" + name] = {"norms_per_s": 4096 / (t_graph * 1e-3), "ms_per_batch": t_graph,
+                                "elements": int(off[-1]), "GBps": off[-1] * x.element_size() / (t_graph * 1e-3) / 1e9,
+                                "one_launch_per_vector_ms": t_single,
+                                "one_launch_per_vector_norms_per_s": 4096 / (t_single * 1e-3),
+                                "bitwise_equal_to_single": same}
+        g.close()
+        del x
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2509_06220_gb300 as nrm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            t = torch.zeros(1, device=dev)
+            pg.all_reduce(t)
+        torch.cuda.synchronize()
+
+    ctx = nrm.context(local)
+    seed = 1 + rank
+    xd = nrm.nrm_gen(N, seed, 0, torch.float64, device=dev)
+    xs = nrm.nrm_gen(N, seed, 0, torch.float32, device=dev)
+    od = torch.empty((), dtype=torch.float64, device=dev)
+    os_ = torch.empty((), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        nrm.nrmf(xd, out=od, ctx=ctx)
+        nrm.nrmf(xs, out=os_, ctx=ctx)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    launches0 = ctx.launches
+    with ClockSampler(local) as clk:
+        barrier()
+        evs[0].record()
+        for i in range(K):
+            nrm.nrmf(xd, out=od, ctx=ctx)
+            evs[2 * i + 1].record()
+            nrm.nrmf(xs, out=os_, ctx=ctx)
+            evs[2 * i + 2].record()
+        barrier()
+    launches = ctx.launches - launches0
+    total_ms = evs[0].elapsed_time(evs[2 * K])
+    d_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(K)]
+    s_ms = [evs[2 * i + 1].elapsed_time(evs[2 * i + 2]) for i in range(K)]
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / K
+    value = world * K * (BYTES_D + BYTES_S) / (total_ms * 1e-3) / 1e9
+    d_avg = statistics.mean(d_ms)
+    s_avg = statistics.mean(s_ms)
+    clocks = clk.summary()
+
+    peaks = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    sm_max = peaks.get("sm_max_mhz") or 2070.0
+    # FP64 pipe: 152 SMs x 2 FP64 FMA per clock per SM (GB300's 1.25 TFLOP/s
+    # FP64 at the maximum SM clock); the binary64 tree issues F64_PER_HYPOT
+    # FP64-pipe instructions per v1_hypot (ncu count on this kernel, in
+    # profiles/), so its compute ceiling in hypot/s is below.
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_ops_peak = sms * 2 * sm_max * 1e6
+    hypot_d = N - 1
+    d_bytes_gbs = BYTES_D / (d_avg * 1e-3) / 1e9
+    s_bytes_gbs = BYTES_S / (s_avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": d_bytes_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": d_bytes_gbs / hbm_peak, "traffic": None, "kernel": "tree_kernel<double,3,OpHypot>",
+            "peak_source": peak_src + " hbm_gbs", "launch_ms": d_avg}
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "bytes_per_step": BYTES_D + BYTES_S,
+                       "l2": "inputs (3 GiB) exceed the 129 MB L2; no flush", "parallelism": "replicas" if world > 1
+                       else "single GPU"},
+            "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+            "parts": {"dnrmf": {"ms": d_avg, "GBps": d_bytes_gbs, "Gelem_per_s": N / (d_avg * 1e-3) / 1e9,
+                                "Ghypot_per_s": hypot_d / (d_avg * 1e-3) / 1e9,
+                                "fp64_pipe_peak_Gops": fp64_ops_peak / 1e9},
+                      "snrmf": {"ms": s_avg, "GBps": s_bytes_gbs, "Gelem_per_s": N / (s_avg * 1e-3) / 1e9,
+                                "hbm_frac": s_bytes_gbs / hbm_peak}}}
+
+    # end to end through the host-buffer entry point
+    if not args.no_e2e:
+        hd = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        hs = torch.empty(N, dtype=torch.float32, pin_memory=True)
+        hd.copy_(xd)
+        hs.copy_(xs)
+        nrm.nrm_host(hd, ctx=ctx, device=local)
+        nrm.nrm_host(hs, ctx=ctx, device=local)
+        reps = 5
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            vd = nrm.nrm_host(hd, ctx=ctx, device=local)
+            vs = nrm.nrm_host(hs, ctx=ctx, device=local)
+        barrier()
+        te = time.perf_counter() - t0
+        if pg is not None:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            te = float(t.item())
+        line["e2e"] = {"value": world * reps * (BYTES_D + BYTES_S) / te / 1e9, "unit": "GB/s",
+                       "h2d_bytes_per_step": BYTES_D + BYTES_S, "d2h_bytes_per_step": 12,
+                       "ms_per_step": te / reps * 1e3}
+        assert np.float64(vd).tobytes() == np.float64(od.item()).tobytes()
+        del hd, hs
+
+    if not args.no_batch and rank == 0:
+        line["parts"].update(time_batch(nrm, torch, ctx, dev))
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        hxd = xd.cpu().numpy()
+        hxs = xs.cpu().numpy()
+        t0 = time.perf_counter()
+        vd = oracle.nrm(hxd)
+        vs = oracle.nrm(hxs)
+        tc = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": (BYTES_D + BYTES_S) / tc / 1e9, "unit": "GB/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "one full step (FP64 and FP32 vectors of 2^28), single thread, %.1f s" % tc,
+                                "bitwise_equal": bool(vd.tobytes() == np.float64(od.item()).tobytes()
+                                                      and vs.tobytes() == np.float32(os_.item()).tobytes())}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
