@@ -193,6 +193,34 @@ nrm_status nrm_gen(nrm_dtype dtype, void *x, int64_t n, uint64_t seed, uint64_t 
 nrm_status nrm_gen_ragged(nrm_dtype dtype, void *x, int64_t x_len, const int64_t *offsets, int64_t B, uint64_t seed,
                           int32_t emin, int32_t emax, void *stream);
 
+/*
+ * xNRMF in binary64 that allocates nothing (the paper has no counterpart;
+ * this is a deployment variant of nrmf_d).  *out = ||x[0..n)||_F with the
+ * same tree, hence bitwise the same result as nrmf_d.
+ *
+ * For callers that cannot call cudaMalloc: cudaMalloc and cudaFree can
+ * synchronise the whole device, which latency-critical loops cannot afford,
+ * and some applications hand all device memory to their own allocator or to
+ * a fixed budget and forbid allocations outside it.  No context is needed.
+ *   x     : device pointer to n binary64 elements (any element alignment);
+ *   n     : 0 <= n <= NRM_NOALLOC_MAX_N; n == 0 gives +0;
+ *   out   : device pointer to one binary64, written asynchronously;
+ *   stream: cudaStream_t as void* (NULL = legacy default stream).
+ * Scratch: a static device array of about 1 MiB inside the library, created
+ * on every device that loads the library and held until the process exits.
+ * The first call on each device looks up that array's address (with the
+ * device current); make that first call before any stream capture.  All
+ * calls on a device share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * give wrong results -- order them on one stream.
+ * Errors: NRM_EINVAL for out == NULL, n < 0, x == NULL with n > 0, or
+ * n > NRM_NOALLOC_MAX_N (the tree would need more scratch than the array
+ * holds); NRM_EDEVICE if no device is current; NRM_ECUDA if a CUDA call
+ * fails.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+#define NRM_NOALLOC_MAX_N (INT64_C(1) << 29)
+nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, void *stream);
+
 /* Number of tree-kernel launches this context has issued (for accounting). */
 uint64_t nrm_kernel_launches(const nrm_ctx *ctx);
 

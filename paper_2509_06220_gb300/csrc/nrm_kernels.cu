@@ -652,3 +652,114 @@ extern "C" nrm_status nrm_batch(nrm_ctx *ctx, nrm_dtype dtype, const void *x, in
                                 void *stream) {
     return nrm_batch_impl(ctx, dtype, x, x_len, offsets, B, p, out, status, (cudaStream_t)stream);
 }
+
+// ---------------------------------------------------------------------------
+// nrmf_d_noalloc: xNRMF in binary64 without any allocation.
+//
+// Some callers cannot call cudaMalloc: cudaMalloc and cudaFree can
+// synchronise the whole device, which a latency-critical loop cannot
+// afford, and some applications give all device memory to their own
+// allocator or run under a fixed budget that forbids allocations outside it.
+// This entry point therefore needs no context.  Its scratch (the tree's
+// ticket counters and partial-norm slots) is the file-scope array below,
+// created when the library is loaded onto a device and held until the
+// process exits.  It is shared by every call on that device and keeps the
+// last call's contents; the tickets are cleared on the stream at the start of
+// each call.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NA_DW_MAX = 10;                                // at most 2^10 work items
+constexpr int64_t NA_NODES = (int64_t(1) << NA_DW_MAX) - 1;  // internal tree nodes
+constexpr size_t NA_TICKET_BYTES = 4096;                     // >= NA_NODES * 4, slot-aligned
+constexpr size_t NA_SLOT_BYTES = (size_t)2 * NA_NODES * 512; // one 512-byte row per child node
+constexpr int NA_G = 3, NA_WPB = 8;
+constexpr int NA_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char nrm_noalloc_scratch[NA_TICKET_BYTES + NA_SLOT_BYTES];
+
+struct NaDevice {
+    bool ready = false;
+    unsigned char *scratch = nullptr; // device address of nrm_noalloc_scratch
+    int sms = 0;
+    int occ = 1;
+};
+NaDevice na_devices[NA_MAX_DEVICES];
+std::mutex na_mutex;
+
+// One-time set-up per device, with that device current: look up the
+// device address of the scratch array (host code cannot use the symbol
+// itself) and the occupancy of the kernel.
+nrm_status na_setup(int dev, NaDevice **out) {
+    std::lock_guard<std::mutex> lock(na_mutex);
+    NaDevice &d = na_devices[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, nrm_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return NRM_ECUDA;
+        }
+        e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return NRM_ECUDA;
+        int occ = 0;
+        const size_t smem = (size_t)NA_WPB * MAXL * 512;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<double, NA_G, OpHypot<double>>,
+                                                          NA_WPB * 32, smem);
+        if (e != cudaSuccess) return NRM_ECUDA;
+        d.occ = std::max(1, occ);
+        d.scratch = static_cast<unsigned char *>(p);
+        d.ready = true;
+    }
+    *out = &d;
+    return NRM_OK;
+}
+
+} // namespace
+
+extern "C" nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, void *stream) {
+    if (!out || n < 0 || (n > 0 && !x)) return NRM_EINVAL;
+    if (n > NRM_NOALLOC_MAX_N) return NRM_EINVAL; // the tree would need more scratch than the array holds
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(double), s) == cudaSuccess ? NRM_OK : NRM_ECUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return NRM_EDEVICE;
+    NaDevice *d = nullptr;
+    nrm_status st = na_setup(dev, &d);
+    if (st != NRM_OK) return st;
+
+    // the same tree as nrmf_d; only the cut depth is capped by the scratch size
+    VecPlan pl{};
+    pl.n = n;
+    pl.m = (n + 63) / 64;
+    pl.D = ceil_log2_i64(pl.m);
+    int dw = std::max(pl.D - 7, ceil_log2_i64((int64_t)d->sms * NA_WPB * 2));
+    dw = std::min(dw, pl.D - NA_G);
+    dw = std::max(dw, 0);
+    dw = std::min(dw, NA_DW_MAX);
+    pl.dw = dw;
+    pl.k = pl.D - dw;
+    if (pl.k > NA_G + MAXL) return NRM_EINVAL;
+    const int64_t items = int64_t(1) << dw;
+    const int64_t nodes = items - 1;
+
+    unsigned *tickets = reinterpret_cast<unsigned *>(d->scratch);
+    double *slots = reinterpret_cast<double *>(d->scratch + NA_TICKET_BYTES);
+    if (nodes > 0 && cudaMemsetAsync(tickets, 0, (size_t)nodes * sizeof(unsigned), s) != cudaSuccess)
+        return NRM_ECUDA;
+    TreeArgs<double> a{};
+    a.x = x;
+    a.out = out;
+    a.plans = nullptr;
+    a.one = pl;
+    a.B = 1;
+    a.item_lo = 0;
+    a.item_hi = items;
+    a.tickets = tickets;
+    a.slots = slots;
+    const size_t smem = (size_t)NA_WPB * MAXL * 512;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + NA_WPB - 1) / NA_WPB,
+                                                                  (int64_t)d->sms * d->occ));
+    tree_kernel<double, NA_G, OpHypot<double>><<<(unsigned)blocks, NA_WPB * 32, smem, s>>>(a, OpHypot<double>{});
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
