@@ -205,7 +205,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--log2n", type=int, default=28,
+                    help="vector length 2^k (28 is the benchmark; smaller only for profiling captures)")
     args = ap.parse_args()
+    global N, BYTES_D, BYTES_S
+    N = 1 << args.log2n
+    BYTES_D, BYTES_S = N * 8, N * 4
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
