@@ -42,6 +42,9 @@ METRIC = "DNRMF+SNRMF GB/s at n=2^28 (FP64 2 GiB + FP32 1 GiB per step)"
 WORKLOAD = ("xNRMF of one FP64 and one FP32 vector of n=2^28 each, x_i = s*m*2^e, s=+-1, m uniform in [1,2), "
             "e uniform in [-20,20], seed 1 (+rank)")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# the ncu traffic figures in profiles/ belong to the kernel build they were
+# captured on; set to False whenever the binary64 tree kernel changes
+TRAFFIC_VALID = True
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -279,18 +282,26 @@ def main():
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
     sm_max = peaks.get("sm_max_mhz") or 2070.0
-    # FP64 pipe: 152 SMs x 2 FP64 FMA per clock per SM (GB300's 1.25 TFLOP/s
-    # FP64 at the maximum SM clock); the binary64 tree issues F64_PER_HYPOT
-    # FP64-pipe instructions per v1_hypot (ncu count on this kernel, in
-    # profiles/), so its compute ceiling in hypot/s is below.
+    # Compute roofline of the dominant kernel (binary64 tree): 7 IEEE
+    # operations per v1_hypot (Listing 2's one-statement-one-instruction
+    # count) against GB300's FP64 rate from unit counts and clocks: SMs x 2
+    # FP64 FMA per clock x the maximum SM clock (1.25 TFLOP/s).  The HBM view
+    # of the same kernel is reported in parts.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp64_ops_peak = sms * 2 * sm_max * 1e6
     hypot_d = N - 1
     d_bytes_gbs = BYTES_D / (d_avg * 1e-3) / 1e9
     s_bytes_gbs = BYTES_S / (s_avg * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": d_bytes_gbs, "peak": hbm_peak, "unit": "GB/s",
-            "frac": d_bytes_gbs / hbm_peak, "traffic": None, "kernel": "tree_kernel<double,3,OpHypot>",
-            "peak_source": peak_src + " hbm_gbs", "launch_ms": d_avg}
+    achieved_ops = 7 * hypot_d / (d_avg * 1e-3)
+    # DRAM bytes read+written per launch: ncu capture at n = 2^26 scaled by 4
+    # (traffic is proportional to n); see profiles/tree_kernel_small_2e26_full.md
+    traffic = (537.313024e6 + 8.206848e6) * (N / float(1 << 26)) if TRAFFIC_VALID else None
+    roof = {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": fp64_ops_peak / 1e9,
+            "unit": "Gop/s (FP64, 7 per v1_hypot)", "frac": achieved_ops / fp64_ops_peak, "traffic": traffic,
+            "kernel": "tree_kernel<double,3,OpHypot>", "peak_source": "unit counts x clock (%d SMs x 2 x %.0f MHz)"
+            % (sms, sm_max), "launch_ms": d_avg,
+            "hbm_view": {"achieved": d_bytes_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": d_bytes_gbs / hbm_peak,
+                         "peak_source": peak_src + " hbm_gbs"}}
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32", "data": "synthetic",
