@@ -44,7 +44,7 @@ WORKLOAD = ("xNRMF of one FP64 and one FP32 vector of n=2^28 each, x_i = s*m*2^e
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the ncu traffic figures in profiles/ belong to the kernel build they were
 # captured on; set to False whenever the binary64 tree kernel changes
-TRAFFIC_VALID = True
+TRAFFIC_VALID = False
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -298,8 +298,8 @@ def main():
     traffic = (537.313024e6 + 8.206848e6) * (N / float(1 << 26)) if TRAFFIC_VALID else None
     roof = {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": fp64_ops_peak / 1e9,
             "unit": "Gop/s (FP64, 7 per v1_hypot)", "frac": achieved_ops / fp64_ops_peak, "traffic": traffic,
-            "kernel": "tree_kernel<double,3,OpHypot>", "peak_source": "unit counts x clock (%d SMs x 2 x %.0f MHz)"
-            % (sms, sm_max), "launch_ms": d_avg,
+            "kernel": "tree_kernel<double,%d,OpHypot>" % ctx.tuning_for(nrm.NRM_F64).group_log2,
+            "peak_source": "unit counts x clock (%d SMs x 2 x %.0f MHz)" % (sms, sm_max), "launch_ms": d_avg,
             "hbm_view": {"achieved": d_bytes_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": d_bytes_gbs / hbm_peak,
                          "peak_source": peak_src + " hbm_gbs"}}
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": args.warmup,

@@ -108,9 +108,13 @@ nrm_status nrm_reserve(nrm_ctx *ctx, size_t bytes);
  * tuning (single vector: B = 1, x_len = n). */
 size_t nrm_workspace_bytes(const nrm_ctx *ctx, nrm_dtype dtype, int64_t x_len, int64_t B);
 
+/* Tuning of the binary64 kernels (nrm_get_tuning) / of both element types
+ * (nrm_set_tuning); the _for forms address one element type.  A setter
+ * returns NRM_EINVAL (and keeps the old values) if a field is out of range. */
 nrm_status nrm_get_tuning(const nrm_ctx *ctx, nrm_tuning *t);
-/* Returns NRM_EINVAL (and keeps the old values) if a field is out of range. */
 nrm_status nrm_set_tuning(nrm_ctx *ctx, const nrm_tuning *t);
+nrm_status nrm_get_tuning_for(const nrm_ctx *ctx, nrm_dtype dtype, nrm_tuning *t);
+nrm_status nrm_set_tuning_for(nrm_ctx *ctx, nrm_dtype dtype, const nrm_tuning *t);
 
 /*
  * xNRMF (Section 3, the recommended Z + recursive final reduction, with
@@ -221,6 +225,17 @@ nrm_status nrm_gen_ragged(nrm_dtype dtype, void *x, int64_t x_len, const int64_t
 #define NRM_NOALLOC_MAX_N (INT64_C(1) << 29)
 nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, void *stream);
 
+/*
+ * Autotuner: times every tuning candidate (group 2^g rows, warps per block,
+ * work-item depth, residency) on a synthetic problem of the given shape --
+ * one vector of lengths_host[0] elements when B == 1, else a ragged batch
+ * of B vectors with these lengths -- and keeps the fastest for `dtype` in
+ * ctx (also returned in *best when best != NULL).  Tuning never changes a
+ * result bit.  Allocates temporary device memory for the synthetic input;
+ * synchronous.  Errors: NRM_EINVAL (bad arguments), NRM_ENOMEM, NRM_ECUDA.
+ */
+nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t *lengths_host, int64_t B, nrm_tuning *best);
+
 /* Number of tree-kernel launches this context has issued (for accounting). */
 uint64_t nrm_kernel_launches(const nrm_ctx *ctx);
 
@@ -228,6 +243,16 @@ uint64_t nrm_kernel_launches(const nrm_ctx *ctx);
  * workspace or staging allocations of any context fail with NRM_ENOMEM
  * without calling cudaMalloc.  count <= 0 disarms it. */
 void nrm_test_inject_alloc_failures(int count);
+
+/* Test hook: evaluate the binary64 v1_hypot two ways on n generated operand
+ * pairs (family `mode`, 0..6: moderate exponent gaps, close values, edge
+ * significands, raw bit patterns, extreme exponents, gaps near 2^-27, equal
+ * values) -- the integer/FP32 form the tree kernels use and the FP64-pipe
+ * form -- and add the number of bitwise differences to *bad (device
+ * pointer); example (device, 4 doubles) receives the first differing
+ * x, y and both results. */
+nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad, double *example,
+                                void *stream);
 
 /* Test hook: copy the first `count` ticket counters of the context's
  * workspace to host memory (synchronous).  Between calls they are all zero. */

@@ -70,6 +70,8 @@ def load():
         "nrm_workspace_bytes": (sz, [vp, i32, i64, i64]),
         "nrm_get_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
         "nrm_set_tuning": (st, [vp, ctypes.POINTER(Tuning)]),
+        "nrm_get_tuning_for": (st, [vp, i32, ctypes.POINTER(Tuning)]),
+        "nrm_set_tuning_for": (st, [vp, i32, ctypes.POINTER(Tuning)]),
         "nrmf_s": (st, [vp, vp, i64, vp, vp]),
         "nrmf_d": (st, [vp, vp, i64, vp, vp]),
         "nrmp_s": (st, [vp, vp, i64, ctypes.c_float, vp, vp]),
@@ -82,6 +84,7 @@ def load():
         "nrm_gen": (st, [i32, vp, i64, u64, u64, i64, i32, i32, vp]),
         "nrm_gen_ragged": (st, [i32, vp, i64, vp, i64, u64, i32, i32, vp]),
         "nrm_kernel_launches": (u64, [vp]),
+        "nrm_autotune": (st, [vp, i32, vp, i64, ctypes.POINTER(Tuning)]),
         "nrm_test_inject_alloc_failures": (None, [ctypes.c_int]),
         "nrm_test_read_tickets": (st, [vp, vp, i64]),
     }
@@ -148,13 +151,29 @@ class Context:
         self.check(load().nrm_get_tuning(self.h, ctypes.byref(t)), "nrm_get_tuning")
         return t
 
-    def set_tuning(self, group_log2=None, warps_per_block=None, item_log2=None, blocks_per_sm=None):
-        t = self.tuning
-        for k, v in (("group_log2", group_log2), ("warps_per_block", warps_per_block),
-                     ("item_log2", item_log2), ("blocks_per_sm", blocks_per_sm)):
-            if v is not None:
-                setattr(t, k, int(v))
-        self.check(load().nrm_set_tuning(self.h, ctypes.byref(t)), "nrm_set_tuning")
+    def tuning_for(self, dtype):
+        t = Tuning()
+        self.check(load().nrm_get_tuning_for(self.h, dtype, ctypes.byref(t)), "nrm_get_tuning_for")
+        return t
+
+    def set_tuning(self, group_log2=None, warps_per_block=None, item_log2=None, blocks_per_sm=None, dtype=None):
+        """Set tuning fields (None keeps a field); dtype None = both types."""
+        for dt in ((NRM_F32, NRM_F64) if dtype is None else (dtype,)):
+            t = self.tuning_for(dt)
+            for k, v in (("group_log2", group_log2), ("warps_per_block", warps_per_block),
+                         ("item_log2", item_log2), ("blocks_per_sm", blocks_per_sm)):
+                if v is not None:
+                    setattr(t, k, int(v))
+            self.check(load().nrm_set_tuning_for(self.h, dt, ctypes.byref(t)), "nrm_set_tuning_for")
+
+    def autotune(self, dtype, lengths):
+        """Pick the fastest tuning for `dtype` on vectors of these lengths
+        (one length: the single-vector path; several: the ragged batch)."""
+        L = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64).reshape(-1))
+        t = Tuning()
+        self.check(load().nrm_autotune(self.h, dtype, ctypes.c_void_p(L.ctypes.data), L.size, ctypes.byref(t)),
+                   "nrm_autotune")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     def reserve(self, nbytes):
         self.check(load().nrm_reserve(self.h, int(nbytes)), "nrm_reserve")

@@ -376,7 +376,9 @@ extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, device);
     c->sms = prop.multiProcessorCount;
-    c->tune = nrm_tuning{3, 8, 7, 4};
+    // defaults from a sweep on GB300 at n = 2^28 (the autotuner refines them)
+    c->tune[NRM_F32] = nrm_tuning{2, 8, 7, 8};
+    c->tune[NRM_F64] = nrm_tuning{2, 4, 7, 8};
     nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20, 1 << 16);
     if (s != NRM_OK) {
         delete c;
@@ -420,19 +422,36 @@ extern "C" nrm_status nrm_reserve(nrm_ctx *ctx, size_t bytes) {
     return nrm_ctx_ensure(ctx, bytes, (int64_t)(bytes / 1024) + 1);
 }
 
+static bool tuning_ok(const nrm_tuning *t) {
+    if (t->group_log2 < 2 || t->group_log2 > 3) return false;
+    if (t->warps_per_block != 4 && t->warps_per_block != 8 && t->warps_per_block != 16) return false;
+    if (t->item_log2 < t->group_log2 || t->item_log2 > t->group_log2 + MAXL) return false;
+    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 16) return false;
+    return true;
+}
+
 extern "C" nrm_status nrm_get_tuning(const nrm_ctx *ctx, nrm_tuning *t) {
     if (!ctx || !t) return NRM_EINVAL;
-    *t = ctx->tune;
+    *t = ctx->tune[NRM_F64];
     return NRM_OK;
 }
 
 extern "C" nrm_status nrm_set_tuning(nrm_ctx *ctx, const nrm_tuning *t) {
-    if (!ctx || !t) return NRM_EINVAL;
-    if (t->group_log2 < 2 || t->group_log2 > 3) return NRM_EINVAL;
-    if (t->warps_per_block != 4 && t->warps_per_block != 8 && t->warps_per_block != 16) return NRM_EINVAL;
-    if (t->item_log2 < t->group_log2 || t->item_log2 > t->group_log2 + MAXL) return NRM_EINVAL;
-    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 16) return NRM_EINVAL;
-    ctx->tune = *t;
+    if (!ctx || !t || !tuning_ok(t)) return NRM_EINVAL;
+    ctx->tune[NRM_F32] = *t;
+    ctx->tune[NRM_F64] = *t;
+    return NRM_OK;
+}
+
+extern "C" nrm_status nrm_get_tuning_for(const nrm_ctx *ctx, nrm_dtype dtype, nrm_tuning *t) {
+    if (!ctx || !t || (dtype != NRM_F32 && dtype != NRM_F64)) return NRM_EINVAL;
+    *t = ctx->tune[dtype];
+    return NRM_OK;
+}
+
+extern "C" nrm_status nrm_set_tuning_for(nrm_ctx *ctx, nrm_dtype dtype, const nrm_tuning *t) {
+    if (!ctx || !t || (dtype != NRM_F32 && dtype != NRM_F64) || !tuning_ok(t)) return NRM_EINVAL;
+    ctx->tune[dtype] = *t;
     return NRM_OK;
 }
 
@@ -450,14 +469,15 @@ extern "C" nrm_status nrm_test_read_tickets(const nrm_ctx *ctx, uint32_t *host, 
 // are enough work items to fill the GPU (at least min_items when the tree is
 // deep enough) but items no smaller than 2^G rows and no more than 2^DW_MAX.
 static bool plan_single(const nrm_ctx *c, int64_t n, int P, VecPlan &pl) {
+    const nrm_tuning &tu = c->tune[P == 64 ? NRM_F64 : NRM_F32];
     pl = VecPlan{};
     pl.n = n;
     pl.m = (n + P - 1) / P;
     pl.D = ceil_log2_i64(pl.m);
-    const int G = c->tune.group_log2;
-    const int64_t min_items = (int64_t)c->sms * c->tune.warps_per_block * 2;
+    const int G = tu.group_log2;
+    const int64_t min_items = (int64_t)c->sms * tu.warps_per_block * 2;
     int dw_fill = ceil_log2_i64(min_items);
-    int dw = std::max(pl.D - c->tune.item_log2, dw_fill);
+    int dw = std::max(pl.D - tu.item_log2, dw_fill);
     dw = std::min(dw, pl.D - G);
     dw = std::max(dw, 0);
     dw = std::min(dw, DW_MAX);
@@ -468,20 +488,25 @@ static bool plan_single(const nrm_ctx *c, int64_t n, int P, VecPlan &pl) {
     return true;
 }
 
+template <typename T> static const nrm_tuning &tune_of(const nrm_ctx *c) {
+    return c->tune[sizeof(T) == 8 ? NRM_F64 : NRM_F32];
+}
+
 template <typename T, class Op>
 static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, int64_t grid_warps,
                                cudaStream_t s) {
-    const int wpb = c->tune.warps_per_block;
+    const nrm_tuning &tu = tune_of<T>(c);
+    const int wpb = tu.warps_per_block;
     const size_t smem = (size_t)wpb * MAXL * 512; // per-warp counter stacks
     int occ = 0;
     int64_t blocks = 0;
     cudaError_t e = cudaSuccess;
-    switch (c->tune.group_log2) {
+    switch (tu.group_log2) {
 #define NRM_LAUNCH_G(GG)                                                                                    \
     case GG: {                                                                                              \
         cudaFuncSetAttribute(tree_kernel<T, GG, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<T, GG, Op>, wpb * 32, smem);       \
-        occ = std::max(1, std::min(occ, c->tune.blocks_per_sm));                                            \
+        occ = std::max(1, std::min(occ, tu.blocks_per_sm));                                                \
         blocks = std::max<int64_t>(1, std::min<int64_t>((grid_warps + wpb - 1) / wpb, (int64_t)c->sms * occ)); \
         tree_kernel<T, GG, Op><<<(unsigned)blocks, wpb * 32, smem, s>>>(a, op);                             \
         e = cudaGetLastError();                                                                             \
@@ -578,7 +603,7 @@ extern "C" nrm_status nrmp_d(nrm_ctx *ctx, const double *x, int64_t n, double p,
 
 static int64_t batch_nodes_bound(const nrm_ctx *c, int64_t x_len, int64_t B, int P) {
     // sum over vectors of 2^dw - 1 < 2 (m_v / 2^k) summed, m_v <= n_v/P + 1
-    const int k = c->tune.item_log2;
+    const int k = c->tune[P == 64 ? NRM_F64 : NRM_F32].item_log2;
     const int64_t rows = x_len / P + B + 1;
     return (2 * rows >> k) + 2;
 }
@@ -614,8 +639,9 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     VecPlan *plans = reinterpret_cast<VecPlan *>(ws + L.plans);
     int64_t *totals = reinterpret_cast<int64_t *>(ws + L.totals);
     unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + L.cursor);
-    const int kmax = c->tune.group_log2 + MAXL;
-    plan_kernel<T><<<1, 1024, 0, s>>>(off, B, x_len, c->tune.item_log2, DW_MAX, kmax, nodes_bound, plans, totals,
+    const nrm_tuning &tu = tune_of<T>(c);
+    const int kmax = tu.group_log2 + MAXL;
+    plan_kernel<T><<<1, 1024, 0, s>>>(off, B, x_len, tu.item_log2, DW_MAX, kmax, nodes_bound, plans, totals,
                                       cursor, out, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_err(c, e, "plan_kernel launch");
@@ -628,7 +654,7 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     a.cursor = cursor;
     a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>(ws + L.slots);
-    const int64_t persistent = (int64_t)c->sms * 64 * c->tune.warps_per_block; // capped by occupancy
+    const int64_t persistent = (int64_t)c->sms * 64 * tu.warps_per_block; // capped by occupancy
     e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, persistent, s); });
     return set_cuda_err(c, e, "tree_kernel launch (batch)");
 }
@@ -761,5 +787,106 @@ extern "C" nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, vo
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + NA_WPB - 1) / NA_WPB,
                                                                   (int64_t)d->sms * d->occ));
     tree_kernel<double, NA_G, OpHypot<double>><<<(unsigned)blocks, NA_WPB * 32, smem, s>>>(a, OpHypot<double>{});
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// test hook: k1_exact (binary64 v1_hypot without the FP64 pipe) against the
+// FP64 k1 on generated operand pairs; counts bitwise differences
+// (two NaNs count as equal).
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ uint64_t th_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double th_make(uint64_t sign, int64_t biased_exp, uint64_t frac) {
+    return __longlong_as_double((long long)((sign << 63) | ((uint64_t)biased_exp << 52) | (frac & 0x000fffffffffffffull)));
+}
+
+__device__ __forceinline__ uint64_t th_frac(uint64_t u, int kind) {
+    switch (kind & 7) {
+    case 0: return 0;
+    case 1: return 0x000fffffffffffffull;
+    case 2: return 1;
+    case 3: return 1ull << 51;
+    case 4: return u | 0xfffffull;          // low bits all ones
+    case 5: return u & ~0xfffffull;         // low bits all zeros
+    case 6: return 0x000fffffffffffffull - (u & 0xff);
+    default: return u;
+    }
+}
+
+__global__ void k1d_compare_kernel(uint64_t seed, int64_t n, int mode, unsigned long long *bad, double *example) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t u1 = th_mix(seed + (uint64_t)(4 * i + 1) * 0x9E3779B97F4A7C15ull);
+        const uint64_t u2 = th_mix(seed + (uint64_t)(4 * i + 2) * 0x9E3779B97F4A7C15ull);
+        const uint64_t u3 = th_mix(seed + (uint64_t)(4 * i + 3) * 0x9E3779B97F4A7C15ull);
+        double x, y;
+        const int64_t e1 = 1023 - 40 + (int64_t)(u3 % 81);
+        switch (mode) {
+        case 0: { // moderate: exponent gap 0..32
+            const int64_t dd = (int64_t)((u3 >> 20) % 33);
+            x = th_make(u1 >> 63, e1, u1);
+            y = th_make(u2 >> 63, e1 - dd, u2);
+            break;
+        }
+        case 1: { // close values: gap -1, 0, +1
+            const int64_t dd = (int64_t)((u3 >> 20) % 3) - 1;
+            x = th_make(u1 >> 63, e1, u1);
+            y = th_make(u2 >> 63, e1 + dd, ((u3 >> 30) & 1) ? (u1 + ((u2 >> 40) - (1ull << 23))) : u2);
+            break;
+        }
+        case 2: { // edge significands, gap 0..30
+            const int64_t dd = (int64_t)((u3 >> 20) % 31);
+            x = th_make(u1 >> 63, e1, th_frac(u1, (int)(u3 >> 40)));
+            y = th_make(u2 >> 63, e1 - dd, th_frac(u2, (int)(u3 >> 44)));
+            break;
+        }
+        case 3: // raw bit patterns: every class (inf, NaN, subnormal, zero, extremes)
+            x = __longlong_as_double((long long)u1);
+            y = __longlong_as_double((long long)(((u3 >> 10) & 1) ? u2 : (u1 ^ (u2 & 0xffffull))));
+            break;
+        case 4: { // extremes: near the largest and the smallest normal exponent
+            const int64_t ex = ((u3 >> 9) & 1) ? 2046 - (int64_t)((u3 >> 12) % 4) : 1 + (int64_t)((u3 >> 12) % 4);
+            const int64_t dd = (int64_t)((u3 >> 20) % 31);
+            x = th_make(0, ex, u1);
+            y = th_make(0, ex - dd > 0 ? ex - dd : 0, u2);
+            break;
+        }
+        case 5: { // gaps around the S = 1 shortcut
+            const int64_t dd = 25 + (int64_t)((u3 >> 20) % 5);
+            x = th_make(0, e1, th_frac(u1, (int)(u3 >> 40)));
+            y = th_make(0, e1 - dd, th_frac(u2, (int)(u3 >> 44)));
+            break;
+        }
+        default: { // equal or nearly equal values (S near 2)
+            x = th_make(0, e1, u1);
+            y = th_make(0, e1, u1 - (u2 & 0x3ff) + ((u2 >> 12) & 0x3ff));
+            break;
+        }
+        }
+        const double a = k1_exact(x, y), b = k1(x, y);
+        const bool same = (__double_as_longlong(a) == __double_as_longlong(b)) || (isnan(a) && isnan(b));
+        if (!same) {
+            if (atomicAdd(bad, 1ull) == 0ull) {
+                example[0] = x;
+                example[1] = y;
+                example[2] = a;
+                example[3] = b;
+            }
+        }
+    }
+}
+
+} // namespace
+
+extern "C" nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad,
+                                           double *example, void *stream) {
+    if (n < 0 || !bad || !example) return NRM_EINVAL;
+    k1d_compare_kernel<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(seed, n, mode, bad, example);
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }

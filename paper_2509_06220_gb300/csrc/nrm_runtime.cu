@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <vector>
 
 #include "../../include/nrm.h"
 #include "nrm_device.cuh"
@@ -194,4 +195,75 @@ extern "C" nrm_status nrm_host(nrm_ctx *ctx, nrm_dtype dtype, const void *x_host
         return NRM_ECUDA;
     }
     return NRM_OK;
+}
+
+// --- autotuner -------------------------------------------------------------
+// Times every tuning candidate on a synthetic problem of the caller's shape
+// and keeps the fastest for that element type.  Candidates only change how
+// the fixed tree is mapped onto warps, never a result bit.
+extern "C" nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t *lengths_host, int64_t B,
+                                   nrm_tuning *best_out) {
+    if (!ctx || !lengths_host || B < 1 || (dtype != NRM_F32 && dtype != NRM_F64)) return NRM_EINVAL;
+    std::vector<int64_t> off((size_t)B + 1, 0);
+    for (int64_t i = 0; i < B; ++i) {
+        if (lengths_host[i] < 0) return NRM_EINVAL;
+        off[(size_t)i + 1] = off[(size_t)i] + lengths_host[i];
+    }
+    const int64_t total = off[(size_t)B];
+    const size_t es = dtype == NRM_F64 ? 8 : 4;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return NRM_ECUDA;
+    void *x = nullptr, *out = nullptr;
+    int64_t *offd = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    nrm_status st = NRM_OK;
+    if (cudaMalloc(&x, (size_t)std::max<int64_t>(total, 1) * es) != cudaSuccess ||
+        cudaMalloc(&out, (size_t)B * es) != cudaSuccess ||
+        cudaMalloc((void **)&offd, (size_t)(B + 1) * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        st = NRM_ENOMEM;
+    }
+    if (st == NRM_OK) {
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaMemcpyAsync(offd, off.data(), (size_t)(B + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        st = nrm_gen_ragged(dtype, x, total, offd, B, 0x5eedull, -20, 20, s);
+    }
+    const nrm_tuning saved = ctx->tune[dtype];
+    nrm_tuning best = saved;
+    float best_ms = 1e30f;
+    auto run = [&](void) -> nrm_status {
+        if (B == 1) return nrm_run_single_range(ctx, dtype, x, total, 2.0, out, s, nullptr, 0, 0);
+        return nrm_batch_impl(ctx, dtype, x, total, offd, B, 2.0, out, nullptr, s);
+    };
+    for (int G = 2; G <= 3 && st == NRM_OK; ++G)
+        for (int wpb : {4, 8, 16})
+            for (int k = G + 3; k <= G + 6 && st == NRM_OK; ++k)
+                for (int bps : {2, 4, 8}) {
+                    ctx->tune[dtype] = nrm_tuning{G, wpb, k, bps};
+                    if (total == 0) break;
+                    st = run(); // warm-up (and workspace growth)
+                    if (st != NRM_OK) break;
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < 3 && st == NRM_OK; ++r) st = run();
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) st = NRM_ECUDA;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (st == NRM_OK && ms < best_ms) {
+                        best_ms = ms;
+                        best = ctx->tune[dtype];
+                    }
+                }
+    ctx->tune[dtype] = (st == NRM_OK) ? best : saved;
+    if (s) cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (x) cudaFree(x);
+    if (out) cudaFree(out);
+    if (offd) cudaFree(offd);
+    if (best_out) *best_out = ctx->tune[dtype];
+    return st;
 }

@@ -479,3 +479,48 @@ def test_tickets_return_to_zero(nrm):
         assert not t.any(), np.nonzero(t)[0][:20]
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("mode", range(7))
+def test_k1_exact_matches_fp64_k1(nrm, mode):
+    """The binary64 tree computes v1_hypot with integer/FP32 arithmetic
+    (GB300's FP64 pipe is the bottleneck otherwise); it must equal the FP64
+    v1_hypot of Listing 2 bit for bit.  2^30 generated pairs per family:
+    moderate exponent gaps, close values, edge significands, raw bit patterns
+    (inf, NaN, subnormal, zero), extreme exponents (overflow to inf), gaps
+    around the 2^-27 shortcut, equal values."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_k1d_compare
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    bad = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ex = torch.zeros(4, dtype=torch.float64, device=DEV)
+    for rep in range(4):
+        assert f(1234567 + 1000 * mode + rep, 1 << 28, mode, ctypes.c_void_p(bad.data_ptr()),
+                 ctypes.c_void_p(ex.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0, ex.cpu().numpy()
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_autotune_keeps_bits(nrm, dt):
+    """The autotuner picks a valid tuning; results before and after are
+    bitwise identical (single vector and ragged batch)."""
+    ctx = nrm.Context(0)
+    try:
+        code = nrm.NRM_F64 if dt == np.float64 else nrm.NRM_F32
+        x = inputs.vector(3 * (1 << 20) + 17, seed=19, vec=0, dtype=dt)
+        xd = dev(x)
+        before = nrm.nrmf(xd, ctx=ctx).item()
+        best = ctx.autotune(code, [x.size])
+        assert 2 <= best["group_log2"] <= 3 and best["warps_per_block"] in (4, 8, 16)
+        after = nrm.nrmf(xd, ctx=ctx).item()
+        assert bits_equal(np.asarray(before, dt), np.asarray(after, dt))
+        assert bits_equal(np.asarray(after, dt), oracle.nrm(x))
+        xb, off = inputs.ragged_batch(256, seed=20, dtype=dt, max_log2=14)
+        ctx.autotune(code, np.diff(off))
+        out, _ = nrm.nrm_batch(dev(xb), dev(off), ctx=ctx)
+        assert bits_equal(out.cpu().numpy(), oracle.nrm_batch(xb, off))
+    finally:
+        ctx.close()
