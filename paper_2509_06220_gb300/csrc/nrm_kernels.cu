@@ -95,8 +95,11 @@ __device__ __forceinline__ void load_slot(const T *src, T (&r)[Geo<T>::V]) {
     }
 }
 
+// The register cap comes from the combine (Op::kMaxRegs): the trees are
+// latency-bound, so more resident warps pay more than per-thread ILP (a
+// sweep on GB300 found 64 registers best for v1_hypot in both precisions).
 template <typename T, int G, class Op>
-__global__ void __launch_bounds__(512) tree_kernel(TreeArgs<T> a, Op op) {
+__global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
     constexpr int V = Geo<T>::V;
     constexpr int P = Geo<T>::P;
     const int lane = threadIdx.x & 31;
@@ -377,8 +380,8 @@ extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
     cudaGetDeviceProperties(&prop, device);
     c->sms = prop.multiProcessorCount;
     // defaults from a sweep on GB300 at n = 2^28 (the autotuner refines them)
-    c->tune[NRM_F32] = nrm_tuning{2, 8, 7, 8};
-    c->tune[NRM_F64] = nrm_tuning{2, 4, 7, 8};
+    c->tune[NRM_F32] = nrm_tuning{3, 8, 7, 4};
+    c->tune[NRM_F64] = nrm_tuning{2, 4, 7, 16};
     nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20, 1 << 16);
     if (s != NRM_OK) {
         delete c;
@@ -699,7 +702,7 @@ constexpr int NA_DW_MAX = 10;                                // at most 2^10 wor
 constexpr int64_t NA_NODES = (int64_t(1) << NA_DW_MAX) - 1;  // internal tree nodes
 constexpr size_t NA_TICKET_BYTES = 4096;                     // >= NA_NODES * 4, slot-aligned
 constexpr size_t NA_SLOT_BYTES = (size_t)2 * NA_NODES * 512; // one 512-byte row per child node
-constexpr int NA_G = 3, NA_WPB = 8;
+constexpr int NA_G = 2, NA_WPB = 4;
 constexpr int NA_MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char nrm_noalloc_scratch[NA_TICKET_BYTES + NA_SLOT_BYTES];
