@@ -163,6 +163,16 @@ nrm_status nrm_batch(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len
                      int64_t B, double p, void *out, int32_t *status, void *stream);
 
 /*
+ * Batch of segments: out[i] = ||x[starts[i] .. starts[i] + lengths[i])||_p
+ * (device arrays of B int64 each), the same tree and guarantees as
+ * nrm_batch; segments may lie anywhere in x (a device arena) and in any
+ * order.  A segment with starts[i] < 0, lengths[i] < 0 or starts[i] +
+ * lengths[i] > x_len gives NaN and NRM_EINVAL in status[i].
+ */
+nrm_status nrm_batch_segments(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *starts,
+                              const int64_t *lengths, int64_t B, double p, void *out, int32_t *status, void *stream);
+
+/*
  * The same batch captured once into a CUDA graph (plan kernel + tree
  * kernel) and replayed with nrm_graph_launch; each replay reads the current
  * contents of x and offsets.  The context's workspace is sized for x_len and
@@ -235,6 +245,61 @@ nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, void *stream)
  * synchronous.  Errors: NRM_EINVAL (bad arguments), NRM_ENOMEM, NRM_ECUDA.
  */
 nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t *lengths_host, int64_t B, nrm_tuning *best);
+
+/*
+ * Continuous-batching server.  Requests (element type, p, length; input
+ * copied from the host or generated on the device) are submitted at any
+ * time; a worker thread admits them in FIFO order as soon as their input
+ * fits in the device arena, and launches steps on `nstreams` streams as
+ * they free up, so steps overlap on the device and later arrivals join the
+ * next step.  A step computes up to `max_batch` requests, grouped by (type,
+ * p), with nrm_batch_segments; every result is bitwise the same as the
+ * request computed alone.  The budget covers the input arena and the
+ * streams' tree workspaces, which are reserved at creation (the loop never
+ * allocates).  Latency is measured from arrival to the result on the host.
+ */
+typedef struct nrm_srv nrm_srv;
+
+typedef struct {
+    nrm_dtype dtype;       /* NRM_F32 or NRM_F64 */
+    int32_t emin, emax;    /* device-generated input: exponent range of nrm_gen */
+    double p;              /* > 0; 2 = xNRMF */
+    int64_t n;             /* elements */
+    const void *x_host;    /* input on the host (copied at launch), or NULL: */
+    uint64_t seed;         /*   generate with nrm_gen(seed, vector id = request id) */
+    double arrival_s;      /* nrm_srv_replay only: arrival time from the trace start */
+} nrm_request;
+
+typedef struct {
+    int64_t submitted, admitted, rejected, completed;
+    int64_t steps, launches;     /* steps launched; kernel launches (2 per group) */
+    int64_t max_queue;           /* most requests waiting for memory at once */
+    int64_t peak_bytes, arena_bytes;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* arrival -> result on the host */
+    double wall_s, norms_per_s, elements_per_s;
+} nrm_srv_report;
+
+/* Create a server on `device` with a device-memory budget (bytes, inputs +
+ * workspaces), nstreams in 1..16, max_batch >= 1 requests per step.
+ * NRM_EBUDGET if the workspaces leave no room for inputs. */
+nrm_status nrm_srv_create(nrm_srv **srv, int device, size_t budget_bytes, int nstreams, int max_batch);
+/* Submit one request; *id receives its id.  NRM_EBUDGET if its input can
+ * never fit the arena (counted as rejected); NRM_EINVAL for bad fields.
+ * A host input must stay valid until the request is done. */
+nrm_status nrm_srv_submit(nrm_srv *srv, const nrm_request *req, uint64_t *id);
+/* *done = 1 once the request finished; then *norm (widened to double) and
+ * *status (NRM_OK or the error) are set. */
+nrm_status nrm_srv_poll(nrm_srv *srv, uint64_t id, double *norm, int32_t *status, int32_t *done);
+/* Wait until every submitted request is done (NRM_ETIMEOUT after timeout_s). */
+nrm_status nrm_srv_drain(nrm_srv *srv, double timeout_s);
+nrm_status nrm_srv_report_get(nrm_srv *srv, nrm_srv_report *rep);
+/* Replay a trace: submit reqs[i] at its arrival_s (busy-waiting on the
+ * host clock), drain, and return each norm and latency (ms) plus the report.
+ * Rejected requests give NaN and latency -1. */
+nrm_status nrm_srv_replay(nrm_srv *srv, const nrm_request *reqs, int64_t count, double *norms, double *latency_ms,
+                          nrm_srv_report *rep);
+/* Stop the worker after the queued requests finish, and free everything. */
+nrm_status nrm_srv_destroy(nrm_srv *srv);
 
 /* Number of tree-kernel launches this context has issued (for accounting). */
 uint64_t nrm_kernel_launches(const nrm_ctx *ctx);

@@ -42,6 +42,22 @@ class Tuning(ctypes.Structure):
                 ("item_log2", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("emin", ctypes.c_int32), ("emax", ctypes.c_int32),
+                ("p", ctypes.c_double), ("n", ctypes.c_int64), ("x_host", ctypes.c_void_p),
+                ("seed", ctypes.c_uint64), ("arrival_s", ctypes.c_double)]
+
+
+class SrvReport(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "admitted", "rejected", "completed", "steps", "launches",
+                                              "max_queue", "peak_bytes", "arena_bytes")] + \
+               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "wall_s", "norms_per_s",
+                                               "elements_per_s")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -85,6 +101,15 @@ def load():
         "nrm_gen_ragged": (st, [i32, vp, i64, vp, i64, u64, i32, i32, vp]),
         "nrm_kernel_launches": (u64, [vp]),
         "nrm_autotune": (st, [vp, i32, vp, i64, ctypes.POINTER(Tuning)]),
+        "nrm_batch_segments": (st, [vp, i32, vp, i64, vp, vp, i64, ctypes.c_double, vp, vp, vp]),
+        "nrm_srv_create": (st, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
+        "nrm_srv_submit": (st, [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "nrm_srv_poll": (st, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_int32)]),
+        "nrm_srv_drain": (st, [vp, ctypes.c_double]),
+        "nrm_srv_report_get": (st, [vp, ctypes.POINTER(SrvReport)]),
+        "nrm_srv_replay": (st, [vp, ctypes.POINTER(Request), i64, vp, vp, ctypes.POINTER(SrvReport)]),
+        "nrm_srv_destroy": (st, [vp]),
         "nrm_test_inject_alloc_failures": (None, [ctypes.c_int]),
         "nrm_test_read_tickets": (st, [vp, vp, i64]),
     }
@@ -354,3 +379,120 @@ def nrm_gen_ragged(offsets, seed=0, dtype=None, emin=-20, emax=20, out=None, str
     if r != NRM_OK:
         raise NrmError(r, "nrm_gen_ragged")
     return out
+
+
+def nrm_batch_segments(x, starts, lengths, p=2.0, out=None, status=None, stream=None, ctx=None):
+    """Norms of x[starts[i] : starts[i] + lengths[i]] (device int64 arrays)."""
+    import torch
+    _check_vec(x)
+    dt = _dtype_code(x)
+    B = starts.numel()
+    c = ctx or context(x.device)
+    if out is None:
+        out = torch.empty(B, dtype=x.dtype, device=x.device)
+    if status is None:
+        status = torch.empty(B, dtype=torch.int32, device=x.device)
+    r = load().nrm_batch_segments(c.h, dt, ctypes.c_void_p(x.data_ptr()), x.numel(),
+                                  ctypes.c_void_p(starts.data_ptr()), ctypes.c_void_p(lengths.data_ptr()), B,
+                                  float(p), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                                  _stream(stream))
+    c.check(r, "nrm_batch_segments")
+    return out, status
+
+
+class Server:
+    """Continuous-batching server (nrm_srv_*): admission under a device
+    memory budget, steps on several streams, p50/p99 latency."""
+
+    def __init__(self, budget_bytes=8 << 30, nstreams=2, max_batch=1024, device=0):
+        h = ctypes.c_void_p()
+        s = load().nrm_srv_create(ctypes.byref(h), int(device), int(budget_bytes), int(nstreams), int(max_batch))
+        if s != NRM_OK:
+            raise NrmError(s, "nrm_srv_create")
+        self.h = h
+        self._keep = []
+
+    def submit(self, n, dtype=NRM_F64, p=2.0, seed=0, emin=-20, emax=20, x_host=None):
+        """Submit one request; the input is x_host (numpy, kept alive until
+        done) or generated on the device from (seed, request id)."""
+        ptr = None
+        if x_host is not None:
+            x_host = np.ascontiguousarray(x_host)
+            self._keep.append(x_host)
+            ptr = x_host.ctypes.data
+            n = x_host.size
+            dtype = NRM_F64 if x_host.dtype == np.float64 else NRM_F32
+        req = Request(int(dtype), int(emin), int(emax), float(p), int(n), ptr, int(seed), 0.0)
+        rid = ctypes.c_uint64()
+        r = load().nrm_srv_submit(self.h, ctypes.byref(req), ctypes.byref(rid))
+        if r != NRM_OK:
+            raise NrmError(r, "nrm_srv_submit")
+        return rid.value
+
+    def poll(self, rid):
+        v, st, done = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+        r = load().nrm_srv_poll(self.h, int(rid), ctypes.byref(v), ctypes.byref(st), ctypes.byref(done))
+        if r != NRM_OK:
+            raise NrmError(r, "nrm_srv_poll")
+        return (v.value, st.value) if done.value else None
+
+    def drain(self, timeout_s=600.0):
+        r = load().nrm_srv_drain(self.h, float(timeout_s))
+        if r != NRM_OK:
+            raise NrmError(r, "nrm_srv_drain")
+
+    def report(self):
+        rep = SrvReport()
+        load().nrm_srv_report_get(self.h, ctypes.byref(rep))
+        return rep.as_dict()
+
+    def replay(self, reqs):
+        """Replay a trace (array of Request with arrival_s); returns
+        (norms, latency_ms, report)."""
+        n = len(reqs)
+        norms = np.zeros(n, np.float64)
+        lat = np.zeros(n, np.float64)
+        rep = SrvReport()
+        r = load().nrm_srv_replay(self.h, reqs, n, ctypes.c_void_p(norms.ctypes.data),
+                                  ctypes.c_void_p(lat.ctypes.data), ctypes.byref(rep))
+        if r != NRM_OK:
+            raise NrmError(r, "nrm_srv_replay")
+        return norms, lat, rep.as_dict()
+
+    def close(self):
+        if self.h:
+            load().nrm_srv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def serving_trace(rate, seconds, seed=0, min_log2=4, max_log2=24, p_probs=(0.8, 0.1, 0.1), ps=(2.0, 1.5, 3.0),
+                  max_requests=None):
+    """Poisson arrivals at `rate` per second for `seconds`; lengths
+    log-uniform in [2^min_log2, 2^max_log2]; FP32/FP64 with probability 1/2;
+    p from `ps` with probabilities `p_probs`.  Returns a ctypes array of
+    Request (inputs generated on the device, keyed by request id)."""
+    from . import inputs
+    count = int(rate * seconds * 1.2) + 16
+    k = inputs.key(seed, 0xFFFFFFF0)
+    u = (inputs.draw(k, np.arange(4 * count, dtype=np.uint64)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    u = u.reshape(count, 4)
+    gaps = -np.log1p(-u[:, 0]) / rate
+    t = np.cumsum(gaps)
+    m = int(np.searchsorted(t, seconds))
+    if max_requests is not None:
+        m = min(m, max_requests)
+    L = np.floor(np.exp2(min_log2 + (max_log2 - min_log2) * u[:m, 1])).astype(np.int64)
+    dts = np.where(u[:m, 2] < 0.5, NRM_F32, NRM_F64)
+    cp = np.cumsum(p_probs)
+    pidx = np.searchsorted(cp, u[:m, 3] * cp[-1], side="right")
+    pv = np.asarray(ps, np.float64)[np.minimum(pidx, len(ps) - 1)]
+    arr = (Request * m)()
+    for i in range(m):
+        arr[i] = Request(int(dts[i]), -20, 20, float(pv[i]), int(L[i]), None, int(seed), float(t[i]))
+    return arr

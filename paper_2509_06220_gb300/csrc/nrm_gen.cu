@@ -97,3 +97,38 @@ extern "C" nrm_status nrm_gen_ragged(nrm_dtype dtype, void *x, int64_t x_len, co
     else gen_ragged_kernel<float><<<blocks, 256, 0, s>>>((float *)x, x_len, offsets, B, seed, emin, span);
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }
+
+// ---------------------------------------------------------------------------
+// segment generator for the server: one launch fills every device-generated
+// request of a step (vector id = request id), same elements as nrm_gen
+// ---------------------------------------------------------------------------
+#include "nrm_internal.h"
+
+uint64_t nrm_gen_key(uint64_t seed, uint64_t vec) { return key_of(seed, vec); }
+
+namespace {
+__global__ void gen_segments_kernel(const NrmGenSeg *segs, const int64_t *cum, int64_t count, int64_t total,
+                                    void *arena) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = count; // last segment with cum <= e
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cum[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const NrmGenSeg sg = segs[lo];
+        const int64_t i = e - cum[lo];
+        const uint64_t u = draw(sg.key, (uint64_t)i);
+        if (sg.dtype == NRM_F64) ((double *)arena)[sg.start + i] = elem_d(u, sg.emin, (uint64_t)sg.span);
+        else ((float *)arena)[sg.start + i] = elem_s(u, sg.emin, (uint64_t)sg.span);
+    }
+}
+} // namespace
+
+nrm_status nrm_gen_segments(const NrmGenSeg *segs_dev, const int64_t *cum_dev, int64_t count, int64_t total,
+                            void *arena, cudaStream_t s) {
+    if (count <= 0 || total <= 0) return NRM_OK;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 32);
+    gen_segments_kernel<<<(unsigned)blocks, 256, 0, s>>>(segs_dev, cum_dev, count, total, arena);
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}

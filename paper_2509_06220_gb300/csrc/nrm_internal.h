@@ -44,9 +44,21 @@ nrm_status nrm_plan_single(const nrm_ctx *c, nrm_dtype dt, int64_t n, nrm::VecPl
 nrm_status nrm_run_single_range(nrm_ctx *c, nrm_dtype dt, const void *x, int64_t n, double p, void *out,
                                 cudaStream_t s, const nrm::VecPlan *pl, int64_t item_lo, int64_t item_hi);
 nrm_status nrm_batch_impl(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
-                          int64_t B, double p, void *out, int32_t *status, cudaStream_t s);
+                          int64_t B, double p, void *out, int32_t *status, cudaStream_t s,
+                          const int64_t *lens = nullptr);
 size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);
 int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);
 void nrm_graph_free(nrm_graph *g);
 void nrm_host_free(nrm_ctx *c);
 bool nrm_test_fail_alloc();
+
+// one device-generated input segment of a server step (element offset in the
+// arena viewed as the segment's type, length, generator key and range)
+struct NrmGenSeg {
+    int64_t start, n;
+    uint64_t key;
+    int32_t emin, span, dtype, pad;
+};
+uint64_t nrm_gen_key(uint64_t seed, uint64_t vec);
+nrm_status nrm_gen_segments(const NrmGenSeg *segs_dev, const int64_t *cum_dev, int64_t count, int64_t total,
+                            void *arena, cudaStream_t s);

@@ -190,8 +190,11 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
 // work items and ticket nodes, statuses, outputs of empty / bad vectors, and
 // the reset of the work cursor
 // ---------------------------------------------------------------------------
+// Vector v is x[off[v] .. off[v+1]) when lens == nullptr (consecutive
+// vectors), else the segment x[off[v] .. off[v] + lens[v]).
 template <typename T>
-__global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ off, int64_t B, int64_t x_len,
+__global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ off, const int64_t *__restrict__ lens,
+                                                    int64_t B, int64_t x_len,
                                                     int kitem, int dwmax, int kmax, int64_t node_cap,
                                                     VecPlan *plans, int64_t *totals, unsigned long long *cursor,
                                                     T *out, int32_t *status) {
@@ -200,8 +203,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     const int tid = threadIdx.x;
     const int64_t per = (B + blockDim.x - 1) / blockDim.x;
     const int64_t v0 = min(B, tid * per), v1 = min(B, v0 + per);
+    int kk = kitem; // work-item depth; deepened below if the tickets would not fit
     auto plan_of = [&](int64_t v, VecPlan &pl, int64_t &items, int64_t &nodes, int32_t &st) {
-        const int64_t a = off[v], b = off[v + 1];
+        const int64_t a = off[v];
+        const int64_t b = lens ? ((lens[v] >= 0 && a <= x_len - lens[v]) ? a + lens[v] : -1) : off[v + 1];
         pl = VecPlan{};
         items = 0;
         nodes = 0;
@@ -216,10 +221,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         if (n == 0) return;
         pl.m = (n + P - 1) / P;
         pl.D = ceil_log2_i64(pl.m);
-        int k = min(pl.D, kitem);
+        int k = min(pl.D, kk);
         if (pl.D - k > dwmax) k = pl.D - dwmax;
         if (k > kmax) {
-            st = NRM_EINVAL; // larger than the tree kernel supports (> 2^35 rows)
+            st = NRM_EINVAL; // larger than the tree kernel supports (> 2^33 rows)
             return;
         }
         pl.k = k;
@@ -227,33 +232,41 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         items = int64_t(1) << pl.dw;
         nodes = items - 1;
     };
-    int64_t si = 0, sn = 0;
-    for (int64_t v = v0; v < v1; ++v) {
-        VecPlan pl;
-        int64_t it, nd;
-        int32_t st;
-        plan_of(v, pl, it, nd, st);
-        si += it;
-        sn += nd;
-    }
-    s_items[tid] = si;
-    s_nodes[tid] = sn;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 partial sums
-    for (int d = 1; d < 1024; d <<= 1) {
-        int64_t ai = 0, an = 0;
-        if (tid >= d) {
-            ai = s_items[tid - d];
-            an = s_nodes[tid - d];
+    int64_t si, sn;
+    for (;;) {
+        si = 0;
+        sn = 0;
+        for (int64_t v = v0; v < v1; ++v) {
+            VecPlan pl;
+            int64_t it, nd;
+            int32_t st;
+            plan_of(v, pl, it, nd, st);
+            si += it;
+            sn += nd;
         }
+        s_items[tid] = si;
+        s_nodes[tid] = sn;
         __syncthreads();
-        s_items[tid] += ai;
-        s_nodes[tid] += an;
+        // Hillis-Steele inclusive scan over the 1024 partial sums
+        for (int d = 1; d < 1024; d <<= 1) {
+            int64_t ai = 0, an = 0;
+            if (tid >= d) {
+                ai = s_items[tid - d];
+                an = s_nodes[tid - d];
+            }
+            __syncthreads();
+            s_items[tid] += ai;
+            s_nodes[tid] += an;
+            __syncthreads();
+        }
+        // segments may overlap, so their nodes are not bounded by x_len:
+        // deeper work items need fewer tickets (the tree is unchanged)
+        if (s_nodes[blockDim.x - 1] <= node_cap || kk >= kmax) break;
         __syncthreads();
+        ++kk;
     }
-    // Offsets that are individually valid but overlap (a decreasing pair in
-    // between) can need more ticket nodes than the workspace was sized for
-    // from x_len; then no vector is computed and all report NRM_ENOMEM.
+    // If even the deepest work items need more ticket nodes than the
+    // workspace holds, no vector is computed and all report NRM_ENOMEM.
     const bool overflow = s_nodes[blockDim.x - 1] > node_cap;
     int64_t ib = s_items[tid] - si, nb = s_nodes[tid] - sn;
     for (int64_t v = v0; v < v1; ++v) {
@@ -604,6 +617,7 @@ extern "C" nrm_status nrmp_d(nrm_ctx *ctx, const double *x, int64_t n, double p,
 
 // batch -----------------------------------------------------------------------
 
+// (for segments that may overlap, the plan kernel's overflow guard applies)
 static int64_t batch_nodes_bound(const nrm_ctx *c, int64_t x_len, int64_t B, int P) {
     // sum over vectors of 2^dw - 1 < 2 (m_v / 2^k) summed, m_v <= n_v/P + 1
     const int k = c->tune[P == 64 ? NRM_F64 : NRM_F32].item_log2;
@@ -631,8 +645,8 @@ extern "C" size_t nrm_workspace_bytes(const nrm_ctx *ctx, nrm_dtype dtype, int64
 }
 
 template <typename T>
-static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t *off, int64_t B, T p, T *out,
-                            int32_t *status, cudaStream_t s) {
+static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t *off, const int64_t *lens,
+                            int64_t B, T p, T *out, int32_t *status, cudaStream_t s) {
     constexpr int P = Geo<T>::P;
     const int64_t nodes_bound = batch_nodes_bound(c, x_len, B, P);
     Layout L = layout_for(nodes_bound, B);
@@ -644,7 +658,7 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + L.cursor);
     const nrm_tuning &tu = tune_of<T>(c);
     const int kmax = tu.group_log2 + MAXL;
-    plan_kernel<T><<<1, 1024, 0, s>>>(off, B, x_len, tu.item_log2, DW_MAX, kmax, nodes_bound, plans, totals,
+    plan_kernel<T><<<1, 1024, 0, s>>>(off, lens, B, x_len, tu.item_log2, DW_MAX, kmax, nodes_bound, plans, totals,
                                       cursor, out, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_err(c, e, "plan_kernel launch");
@@ -663,17 +677,24 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
 }
 
 nrm_status nrm_batch_impl(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
-                          int64_t B, double p, void *out, int32_t *status, cudaStream_t s) {
+                          int64_t B, double p, void *out, int32_t *status, cudaStream_t s, const int64_t *lens) {
     if (!ctx || B < 0 || x_len < 0 || (dtype != NRM_F32 && dtype != NRM_F64)) return NRM_EINVAL;
     if (B > 0 && (!offsets || !out)) return NRM_EINVAL;
     if (x_len > 0 && !x) return NRM_EINVAL;
     if (!(p > 0.0)) return NRM_EINVAL;
     if (B == 0) return NRM_OK;
     if (dtype == NRM_F64)
-        return run_batch<double>(ctx, (const double *)x, x_len, offsets, B, p, (double *)out, status, s);
+        return run_batch<double>(ctx, (const double *)x, x_len, offsets, lens, B, p, (double *)out, status, s);
     const float pf = (float)p;
     if (!(pf > 0.0f)) return NRM_EINVAL;
-    return run_batch<float>(ctx, (const float *)x, x_len, offsets, B, pf, (float *)out, status, s);
+    return run_batch<float>(ctx, (const float *)x, x_len, offsets, lens, B, pf, (float *)out, status, s);
+}
+
+extern "C" nrm_status nrm_batch_segments(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len,
+                                         const int64_t *starts, const int64_t *lengths, int64_t B, double p,
+                                         void *out, int32_t *status, void *stream) {
+    if (B > 0 && !lengths) return NRM_EINVAL;
+    return nrm_batch_impl(ctx, dtype, x, x_len, starts, B, p, out, status, (cudaStream_t)stream, lengths);
 }
 
 extern "C" nrm_status nrm_batch(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len,
