@@ -200,6 +200,30 @@ def time_batch(nrm, torch, ctx, dev):
     return out
 
 
+def time_serving(nrm, seconds, rate):
+    """Serving (config 4): Poisson arrivals at `rate`/s for `seconds`,
+    lengths log-uniform in [2^4, 2^24], FP32/FP64 1:1, p = 2 (80 %) else
+    1.5 or 3; inputs generated on the device at admission; 8 GiB budget.
+    The same trace through the continuous-batching server and through the
+    one-request-per-launch form."""
+    import numpy as np
+    tr = nrm.serving_trace(rate, seconds, seed=0)
+    res, norms = {}, {}
+    for name, (ns, mb) in (("batched", (2, 1024)), ("one_request_per_launch", (1, 1))):
+        srv = nrm.Server(budget_bytes=8 << 30, nstreams=ns, max_batch=mb)
+        v, lat, rep = srv.replay(tr)
+        srv.close()
+        norms[name] = v
+        res[name] = {k: rep[k] for k in ("completed", "rejected", "max_queue", "steps", "launches", "p50_ms",
+                                           "p99_ms", "mean_ms", "max_ms", "wall_s", "norms_per_s", "elements_per_s",
+                                           "peak_bytes", "arena_bytes")}
+    L = np.array([tr[i].n for i in range(len(tr))])
+    res["trace"] = {"rate_per_s": rate, "seconds": seconds, "requests": len(tr), "mean_length": float(L.mean()),
+                    "offered_elements_per_s": float(L.sum() / seconds)}
+    res["bitwise_equal"] = bool(norms["batched"].tobytes() == norms["one_request_per_launch"].tobytes())
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,6 +233,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0,
+                    help="length of the serving trace (config 4 runs 60 s; 0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=50000.0)
     ap.add_argument("--log2n", type=int, default=28,
                     help="vector length 2^k (28 is the benchmark; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -361,6 +388,10 @@ def main():
                                 "sample": "one full step (FP64 and FP32 vectors of 2^28), single thread, %.1f s" % tc,
                                 "bitwise_equal": bool(vd.tobytes() == np.float64(od.item()).tobytes()
                                                       and vs.tobytes() == np.float32(os_.item()).tobytes())}
+    if args.serve_seconds > 0 and rank == 0:
+        del xd, xs
+        torch.cuda.empty_cache()
+        line["parts"]["serve"] = time_serving(nrm, args.serve_seconds, args.serve_rate)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

@@ -34,7 +34,7 @@ struct nrm_ctx {
     // end-to-end (host buffer) staging
     void *stage = nullptr;
     size_t stage_bytes = 0;
-    cudaStream_t s_copy = nullptr, s_comp = nullptr;
+    cudaStream_t s_copy[4] = {nullptr, nullptr, nullptr, nullptr}, s_comp = nullptr;
     std::vector<cudaEvent_t> ev;
     void *out_dev = nullptr;
 };
