@@ -119,6 +119,19 @@ def load_peaks():
         return {}
 
 
+def aggregate(total_ms, world, steps, bytes_per_step, pg=None, device=None):
+    """Whole-job figures across ranks: every rank runs its own problem
+    (weak scaling, no data-path collective); the step time is the MAX over
+    ranks of each rank's timed region and the value counts the bytes of all
+    ranks.  Returns (max_total_ms, value_GBps)."""
+    if pg is not None and world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps * bytes_per_step / (total_ms * 1e-3) / 1e9
+
+
 def run_reference(args):
     """The oracle (plain serial C) on a bounded sample of the workload:
     each step computes xNRMF of the first 2^25 elements of the FP64 and of
@@ -295,12 +308,8 @@ def main():
     total_ms = evs[0].elapsed_time(evs[2 * K])
     d_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(K)]
     s_ms = [evs[2 * i + 1].elapsed_time(evs[2 * i + 2]) for i in range(K)]
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = aggregate(total_ms, world, K, BYTES_D + BYTES_S, pg, dev)
     ms_step = total_ms / K
-    value = world * K * (BYTES_D + BYTES_S) / (total_ms * 1e-3) / 1e9
     d_avg = statistics.mean(d_ms)
     s_avg = statistics.mean(s_ms)
     clocks = clk.summary()

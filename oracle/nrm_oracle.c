@@ -383,15 +383,23 @@ static float comb_apply_s(const comb_s *c, float x, float y)
     }
 }
 
+/* Cut-off p' (Section 4): for p at or above it, pow(Z, 1/p) = 1 for every Z
+ * in [1, 2], so v1_lp returns M = max(|x|, |y|) and xNRMP may switch to the
+ * p = inf code.  For this file's pow the powers of two 2^53 (binary64) and
+ * 2^24 (binary32) are at or above p' (the paper finds 2^52 < p' <= 2^53 for
+ * cr_pow and 2^23 < p' <= 2^24 for cr_powf); the switch changes no bit. */
+#define P_CUT_D 0x1p53
+#define P_CUT_S 0x1p24f
+
 /* Choose the combine for a given p (Section 4): p = 2 is xNRMF (v1_hypot),
- * p = 1 sumabs, p = inf maxabs, any other p > 0 v1_lp with p/2 and 1/p
- * computed once here. */
+ * p = 1 sumabs, p = inf (or p >= the cut-off) maxabs, any other p > 0
+ * v1_lp with p/2 and 1/p computed once here. */
 static comb_d comb_for_d(double p)
 {
     comb_d c = {OP_HYPOT, 0.0, 0.0};
     if (p == 2.0) c.op = OP_HYPOT;
     else if (p == 1.0) c.op = OP_SUMABS;
-    else if (isinf(p)) c.op = OP_MAXABS;
+    else if (p >= P_CUT_D) c.op = OP_MAXABS;
     else { c.op = OP_LP; c.h = p * 0.5; c.ip = 1.0 / p; }
     return c;
 }
@@ -401,7 +409,7 @@ static comb_s comb_for_s(float p)
     comb_s c = {OP_HYPOT, 0.0f, 0.0f};
     if (p == 2.0f) c.op = OP_HYPOT;
     else if (p == 1.0f) c.op = OP_SUMABS;
-    else if (isinf(p)) c.op = OP_MAXABS;
+    else if (p >= P_CUT_S) c.op = OP_MAXABS;
     else { c.op = OP_LP; c.h = p * 0.5f; c.ip = 1.0f / p; }
     return c;
 }

@@ -538,11 +538,15 @@ static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, i
 }
 
 // p -> combine op dispatch (Section 4): 2 -> v1_hypot, 1 -> sumabs,
-// inf -> maxabs, other -> v1_lp with p/2 and 1/p rounded once in T.
+// inf -> maxabs, other -> v1_lp with p/2 and 1/p rounded once in T.  From
+// the cut-off p' on (Section 4) pow(Z, 1/p) is 1 for every Z in [1, 2], so
+// v1_lp returns max(|x|, |y|): p >= 2^53 (binary64) / 2^24 (binary32) takes
+// the maxabs code, which gives the same bits.
 template <typename T, class F> static cudaError_t with_op(T p, F &&f) {
+    const T cut = sizeof(T) == 8 ? T(9007199254740992.0) : T(16777216.0f);
     if (p == T(2)) return f(OpHypot<T>{});
     if (p == T(1)) return f(OpSumAbs<T>{});
-    if (std::isinf(p)) return f(OpMaxAbs<T>{});
+    if (p >= cut) return f(OpMaxAbs<T>{});
     OpLp<T> o;
     o.h = p * T(0.5);
     o.ip = T(1) / p;

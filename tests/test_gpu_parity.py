@@ -124,7 +124,7 @@ def test_sizes_primes_powers(nrm, dt):
 
 
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
-@pytest.mark.parametrize("p", [1.0, 1.5, 3.0, 7.5, 0.5, 2.0 / 3.0, math.inf, math.pi])
+@pytest.mark.parametrize("p", [1.0, 1.5, 3.0, 7.5, 0.5, 2.0 / 3.0, math.inf, math.pi, 2.0 ** 30, 2.0 ** 60])
 def test_pnorm_parity(nrm, dt, p):
     ns = [1, 2, 63, 64, 65, 129, 1000, 8191, 65536, 100003]
     x = inputs.vector(max(ns), seed=4, vec=1, dtype=dt, emin=-8, emax=8)

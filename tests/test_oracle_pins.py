@@ -503,3 +503,45 @@ def test_empty_is_zero():
     """n = 0: +0 (Listing 1 assumes n > 0; +0 is the norm of the empty array)."""
     assert oracle.nrm(np.zeros(0)) == 0.0
     assert oracle.nrm(np.zeros(0, np.float32)) == 0.0
+
+
+@pytest.mark.parametrize("dt,cut", [(np.float64, 2.0 ** 53), (np.float32, 2.0 ** 24)])
+def test_pow_cutoff_p_prime(dt, cut):
+    """Section 4's cut-off p': the smallest p with pow(z, 1/p) = 1 for all z
+    in [1, 2] lies in (2^52, 2^53] (binary64) and (2^23, 2^24] (binary32),
+    the ranges the paper reports for cr_pow / cr_powf; at the cut-off power
+    of two v1_lp returns max(|x|, |y|) bit for bit (so xNRMP may switch to
+    the p = inf code), below it it does not."""
+    one = dt(1.0)
+    two = dt(2.0)
+
+    def is_one(p):
+        return oracle.pow_(two, one / dt(p), dt) == 1.0
+
+    assert not is_one(cut / 2) and is_one(cut)
+    lo, hi = cut / 2, cut  # bisection on the smallest p with pow(2, 1/p) = 1
+    for _ in range(80):
+        mid = dt((lo + hi) / 2)
+        if mid <= lo or mid >= hi:
+            break
+        if is_one(mid):
+            hi = float(mid)
+        else:
+            lo = float(mid)
+    assert cut / 2 < hi <= cut
+    r = random.Random(11)
+    zs = [dt(1 + r.random()) for _ in range(2000)] + [dt(2.0), dt(1.0), np.nextafter(dt(2.0), dt(0))]
+    assert all(oracle.pow_(z, one / dt(cut), dt) == 1.0 for z in zs)
+    diff_below = 0
+    for _ in range(3000):
+        a = dt(r.uniform(0.5, 2) * 2.0 ** r.randint(-30, 30))
+        b = dt(r.uniform(-2, 2) * 2.0 ** r.randint(-30, 30))
+        assert oracle.lp(cut, a, b, dt) == max(abs(a), abs(b))
+        assert oracle.lp(cut * 64, a, b, dt) == max(abs(a), abs(b))
+        assert oracle.lp(cut, a, -a, dt) == abs(a)
+        # below the cut-off, Q^(p/2) vanishes unless |x| = |y|; there Z = 2
+        # and pow(2, 1/p) > 1
+        diff_below += oracle.lp(cut / 4, a, -a, dt) != abs(a)
+    assert diff_below > 2000
+    x = inputs.vector(5000, seed=12, vec=3, dtype=dt)
+    assert oracle.nrm(x, cut) == oracle.nrm(x, math.inf) == np.max(np.abs(x))
