@@ -141,6 +141,31 @@ nrm_status nrmp_s(nrm_ctx *ctx, const float *x, int64_t n, float p, float *out, 
 nrm_status nrmp_d(nrm_ctx *ctx, const double *x, int64_t n, double p, double *out, void *stream);
 
 /*
+ * Strided vector (Section 3 leaves BLAS's incx to future work; done here):
+ * ||(x_0, ..., x_{n-1})||_p with x_i = x[i incx] for incx > 0 and
+ * x_i = x[(n-1-i) |incx|] for incx < 0 (BLAS order: the elements are taken
+ * backwards), by the same tree as nrmp_* on that logical vector.  x is the
+ * lowest-addressed element in both cases.  Errors: NRM_EINVAL for incx == 0
+ * and as nrmp_*.
+ */
+nrm_status nrm_strided(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t n, int64_t incx, double p, void *out,
+                       void *stream);
+
+/*
+ * Norm of a column-major M x N matrix A with leading dimension lda >= M
+ * (Section 3.1): when lda == M (or N == 1) the elements are contiguous and
+ * the matrix is the one vector A[0 .. M N); otherwise the N column norms
+ * are computed (as one segment batch) and their norm by the same tree gives
+ * the result (for any p: ||A||_p^p is the sum of the columns' p-th powers).
+ * Higher-dimensional arrays A(lda, N2, ..., Nk) are the case N = N2...Nk.
+ * out: device pointer to one element.  Uses context scratch of N
+ * (16 + sizeof(element)) bytes.  Errors: NRM_EINVAL for M, N < 0, lda <
+ * max(M, 1), NULL pointers, bad p or dtype.
+ */
+nrm_status nrm_matrix(nrm_ctx *ctx, nrm_dtype dtype, const void *A, int64_t M, int64_t N, int64_t lda, double p,
+                      void *out, void *stream);
+
+/*
  * Ragged batch (the paper's per-column norms of Section 3.1, here for a
  * batch of independent vectors): for i in [0, B),
  *   out[i] = ||x[offsets[i] .. offsets[i+1])||_p

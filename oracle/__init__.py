@@ -44,6 +44,10 @@ def lib():
             "or_nrm_s": (f, [i64, vp, i32, f]),
             "or_nrm_batch_d": (None, [i64, vp, vp, i32, d, vp]),
             "or_nrm_batch_s": (None, [i64, vp, vp, i32, f, vp]),
+            "or_nrm_strided_d": (d, [i64, vp, i64, i32, d]),
+            "or_nrm_strided_s": (f, [i64, vp, i64, i32, f]),
+            "or_nrm_matrix_d": (d, [i64, i64, i64, vp, i32, d]),
+            "or_nrm_matrix_s": (f, [i64, i64, i64, vp, i32, f]),
             "or_nrm_slot_d": (d, [i64, vp, i32, d]),
             "or_nrm_slot_s": (f, [i64, vp, i32, f]),
             "or_ref_q128": (None, [i64, vp, i32, d, i32, pd, pd]),
@@ -127,6 +131,24 @@ def nrm(x, p=2.0, P=None):
         return np.float64(lib().or_nrm_d(a.size, ptr, P or P_D, float(p)))
     a, ptr = _arr(x, np.float32)
     return np.float32(lib().or_nrm_s(a.size, ptr, P or P_S, float(np.float32(p))))
+
+
+def nrm_strided(buf, n, incx, p=2.0, P=None):
+    """Norm of the strided vector over buf (element 0 = lowest address)."""
+    if _is_d(buf):
+        a, ptr = _arr(buf, np.float64)
+        return np.float64(lib().or_nrm_strided_d(n, ptr, incx, P or P_D, float(p)))
+    a, ptr = _arr(buf, np.float32)
+    return np.float32(lib().or_nrm_strided_s(n, ptr, incx, P or P_S, float(np.float32(p))))
+
+
+def nrm_matrix(buf, M, N, lda, p=2.0, P=None):
+    """Norm of the column-major M x N matrix stored in buf with leading dimension lda."""
+    if _is_d(buf):
+        a, ptr = _arr(buf, np.float64)
+        return np.float64(lib().or_nrm_matrix_d(M, N, lda, ptr, P or P_D, float(p)))
+    a, ptr = _arr(buf, np.float32)
+    return np.float32(lib().or_nrm_matrix_s(M, N, lda, ptr, P or P_S, float(np.float32(p))))
 
 
 def nrm_slot(x, p=2.0, P=None):

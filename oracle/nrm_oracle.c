@@ -27,6 +27,8 @@
  *   or_Z_*                 Z_x generalised to p lanes, Listing 4 (Section 3)
  *   or_nrm_*               xNRMF / xNRMP = Z then a final R over the lanes
  *                          (Section 3, recommendation for xNRMF)
+ *   or_nrm_strided_*       a strided vector (BLAS incx, Section 3)
+ *   or_nrm_matrix_*        a matrix with a leading dimension (Section 3.1)
  *   or_nrm_slot_*          the same tree evaluated in "slot form" (a perfect
  *                          tree whose empty slots are skipped); a second,
  *                          independent evaluation used to pin or_nrm_*
@@ -593,6 +595,57 @@ OR_API void or_nrm_batch_d(int64_t B, const int64_t *off, const double *x, int P
 OR_API void or_nrm_batch_s(int64_t B, const int64_t *off, const float *x, int P, float p, float *out)
 {
     for (int64_t i = 0; i < B; ++i) out[i] = or_nrm_s(off[i + 1] - off[i], x + off[i], P, p);
+}
+
+/* Strided vector (Section 3's incx): element i is x[i incx] for incx > 0
+ * and x[(n-1-i) |incx|] for incx < 0 (taken backwards); its norm is the
+ * norm of that logical vector. */
+OR_API double or_nrm_strided_d(int64_t n, const double *x, int64_t incx, int P, double p)
+{
+    if (n <= 0) return 0.0;
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    const int64_t step = incx < 0 ? -incx : incx;
+    for (int64_t i = 0; i < n; ++i) v[i] = incx > 0 ? x[i * step] : x[(n - 1 - i) * step];
+    const double r = or_nrm_d(n, v, P, p);
+    free(v);
+    return r;
+}
+
+OR_API float or_nrm_strided_s(int64_t n, const float *x, int64_t incx, int P, float p)
+{
+    if (n <= 0) return 0.0f;
+    float *v = (float *)malloc(sizeof(float) * (size_t)n);
+    const int64_t step = incx < 0 ? -incx : incx;
+    for (int64_t i = 0; i < n; ++i) v[i] = incx > 0 ? x[i * step] : x[(n - 1 - i) * step];
+    const float r = or_nrm_s(n, v, P, p);
+    free(v);
+    return r;
+}
+
+/* Column-major M x N matrix with leading dimension lda (Section 3.1): with
+ * contiguous storage (lda == M, or one column) it is one vector of M N
+ * elements; otherwise the norms of the N columns are combined, here by the
+ * same tree applied to the vector of column norms. */
+OR_API double or_nrm_matrix_d(int64_t M, int64_t N, int64_t lda, const double *A, int P, double p)
+{
+    if (M <= 0 || N <= 0) return 0.0;
+    if (lda == M || N == 1) return or_nrm_d(M * N, A, P, p);
+    double *c = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int64_t j = 0; j < N; ++j) c[j] = or_nrm_d(M, A + j * lda, P, p);
+    const double r = or_nrm_d(N, c, P, p);
+    free(c);
+    return r;
+}
+
+OR_API float or_nrm_matrix_s(int64_t M, int64_t N, int64_t lda, const float *A, int P, float p)
+{
+    if (M <= 0 || N <= 0) return 0.0f;
+    if (lda == M || N == 1) return or_nrm_s(M * N, A, P, p);
+    float *c = (float *)malloc(sizeof(float) * (size_t)N);
+    for (int64_t j = 0; j < N; ++j) c[j] = or_nrm_s(M, A + j * lda, P, p);
+    const float r = or_nrm_s(N, c, P, p);
+    free(c);
+    return r;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -102,6 +102,8 @@ def load():
         "nrm_kernel_launches": (u64, [vp]),
         "nrm_autotune": (st, [vp, i32, vp, i64, ctypes.POINTER(Tuning)]),
         "nrm_batch_segments": (st, [vp, i32, vp, i64, vp, vp, i64, ctypes.c_double, vp, vp, vp]),
+        "nrm_strided": (st, [vp, i32, vp, i64, i64, ctypes.c_double, vp, vp]),
+        "nrm_matrix": (st, [vp, i32, vp, i64, i64, i64, ctypes.c_double, vp, vp]),
         "nrm_srv_create": (st, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
         "nrm_srv_submit": (st, [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
         "nrm_srv_poll": (st, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
@@ -496,3 +498,39 @@ def serving_trace(rate, seconds, seed=0, min_log2=4, max_log2=24, p_probs=(0.8, 
     for i in range(m):
         arr[i] = Request(int(dts[i]), -20, 20, float(pv[i]), int(L[i]), None, int(seed), float(t[i]))
     return arr
+
+
+def nrm_strided(buf, n, incx, p=2.0, out=None, stream=None, ctx=None):
+    """Norm of the n-element strided vector in the CUDA tensor buf (element
+    0 at buf's start; incx < 0 takes the elements backwards, as BLAS)."""
+    import torch
+    dt = _dtype_code(buf)
+    c = ctx or context(buf.device)
+    if out is None:
+        out = torch.empty((), dtype=buf.dtype, device=buf.device)
+    r = load().nrm_strided(c.h, dt, ctypes.c_void_p(buf.data_ptr()), int(n), int(incx), float(p),
+                           ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    c.check(r, "nrm_strided")
+    return out
+
+
+def nrm_matrix(buf, M, N, lda, p=2.0, out=None, stream=None, ctx=None):
+    """Norm of the column-major M x N matrix stored in the CUDA tensor buf
+    with leading dimension lda (Section 3.1)."""
+    import torch
+    dt = _dtype_code(buf)
+    c = ctx or context(buf.device)
+    if out is None:
+        out = torch.empty((), dtype=buf.dtype, device=buf.device)
+    r = load().nrm_matrix(c.h, dt, ctypes.c_void_p(buf.data_ptr()), int(M), int(N), int(lda), float(p),
+                          ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    c.check(r, "nrm_matrix")
+    return out
+
+
+def nrmf_complex(z, out=None, stream=None, ctx=None):
+    """Frobenius norm of a complex CUDA tensor: |z|^2 = Re^2 + Im^2 (Section 1),
+    so it is xNRMF of the interleaved real view of 2n elements."""
+    import torch
+    r = torch.view_as_real(z.contiguous()).reshape(-1)
+    return nrmf(r, out=out, stream=stream, ctx=ctx)

@@ -27,6 +27,8 @@ struct nrm_ctx {
     size_t ws_bytes = 0;
     unsigned *tickets = nullptr; // one counter per internal tree node; all zero between calls
     int64_t tickets_cap = 0;
+    void *aux = nullptr; // matrix norms: column starts, lengths and norms
+    size_t aux_bytes = 0;
     nrm_tuning tune[2]{}; // per element type: [NRM_F32], [NRM_F64]
     std::string err;
     uint64_t launches = 0;

@@ -135,12 +135,12 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
             pl = a.one;
         }
         const T *xv = a.x + pl.x_off;
-        const bool aligned = ((uintptr_t)xv & 15u) == 0;
+        const bool aligned = pl.stride == 1 && ((uintptr_t)xv & 15u) == 0;
         const uint32_t i = (uint32_t)(gi - pl.item_base);
         const int64_t t = node_rows(pl.m, i, pl.dw);
         const int64_t start = node_start(pl.m, i, pl.dw);
         T r[V];
-        item_tree<T, G, Op>(xv, pl.n, start, t, pl.k, lane, aligned, op, stk, r);
+        item_tree<T, G, Op>(xv, pl.n, start, t, pl.k, lane, aligned, pl.stride, op, stk, r);
 
         // climb the ticket tree above the cut
         uint32_t h = (1u << pl.dw) + i;
@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         const int64_t n = b - a;
         pl.x_off = a;
         pl.n = n;
+        pl.stride = 1;
         if (n == 0) return;
         pl.m = (n + P - 1) / P;
         pl.D = ceil_log2_i64(pl.m);
@@ -413,6 +414,7 @@ extern "C" nrm_status nrm_destroy(nrm_ctx *ctx) {
     nrm_host_free(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->tickets) cudaFree(ctx->tickets);
+    if (ctx->aux) cudaFree(ctx->aux);
     delete ctx;
     return NRM_OK;
 }
@@ -488,6 +490,7 @@ static bool plan_single(const nrm_ctx *c, int64_t n, int P, VecPlan &pl) {
     const nrm_tuning &tu = c->tune[P == 64 ? NRM_F64 : NRM_F32];
     pl = VecPlan{};
     pl.n = n;
+    pl.stride = 1;
     pl.m = (n + P - 1) / P;
     pl.D = ceil_log2_i64(pl.m);
     const int G = tu.group_log2;
@@ -555,10 +558,11 @@ template <typename T, class F> static cudaError_t with_op(T p, F &&f) {
 
 template <typename T>
 static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cudaStream_t s, int64_t item_lo,
-                             int64_t item_hi, const VecPlan *plan_in) {
+                             int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1) {
     VecPlan pl;
     if (plan_in) pl = *plan_in;
     else if (!plan_single(c, n, P_of<T>(), pl)) return NRM_EINVAL;
+    if (!plan_in) pl.stride = stride;
     const int64_t items = int64_t(1) << pl.dw;
     const int64_t nodes = items - 1;
     Layout L = layout_for(nodes, 1);
@@ -617,6 +621,74 @@ extern "C" nrm_status nrmp_s(nrm_ctx *ctx, const float *x, int64_t n, float p, f
 }
 extern "C" nrm_status nrmp_d(nrm_ctx *ctx, const double *x, int64_t n, double p, double *out, void *stream) {
     return nrm_entry<double>(ctx, x, n, p, out, stream);
+}
+
+// strided vectors and matrices (Sections 3 and 3.1) ------------------------------
+
+extern "C" nrm_status nrm_strided(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t n, int64_t incx, double p,
+                                  void *out, void *stream) {
+    if (!ctx || !out || n < 0 || (n > 0 && !x) || incx == 0 || (dtype != NRM_F32 && dtype != NRM_F64))
+        return NRM_EINVAL;
+    if (!(p > 0.0) || (dtype == NRM_F32 && !((float)p > 0.0f))) return NRM_EINVAL;
+    const size_t es = dtype == NRM_F64 ? 8 : 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return set_cuda_err(ctx, cudaMemsetAsync(out, 0, es, s), "cudaMemsetAsync");
+    const int64_t step = incx < 0 ? -incx : incx;
+    if (n > 1 && step > INT64_MAX / (n - 1)) return NRM_EINVAL;
+    // logical element i is x[i incx] (incx > 0) or x[(n-1-i) |incx|] (incx < 0)
+    const char *first = (const char *)x + (incx < 0 ? (size_t)((n - 1) * step) * es : 0);
+    if (dtype == NRM_F64)
+        return run_single<double>(ctx, (const double *)first, n, p, (double *)out, s, 0, 0, nullptr, incx);
+    return run_single<float>(ctx, (const float *)first, n, (float)p, (float *)out, s, 0, 0, nullptr, incx);
+}
+
+namespace {
+__global__ void fill_columns_kernel(int64_t *starts, int64_t *lens, int64_t N, int64_t M, int64_t lda) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        starts[j] = j * lda;
+        lens[j] = M;
+    }
+}
+} // namespace
+
+extern "C" nrm_status nrm_matrix(nrm_ctx *ctx, nrm_dtype dtype, const void *A, int64_t M, int64_t N, int64_t lda,
+                                 double p, void *out, void *stream) {
+    if (!ctx || !out || M < 0 || N < 0 || lda < (M > 1 ? M : 1) || (dtype != NRM_F32 && dtype != NRM_F64))
+        return NRM_EINVAL;
+    if (M > 0 && N > 0 && !A) return NRM_EINVAL;
+    if (!(p > 0.0) || (dtype == NRM_F32 && !((float)p > 0.0f))) return NRM_EINVAL;
+    if (N > 1 && lda > INT64_MAX / N) return NRM_EINVAL;
+    const size_t es = dtype == NRM_F64 ? 8 : 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (M == 0 || N == 0) return set_cuda_err(ctx, cudaMemsetAsync(out, 0, es, s), "cudaMemsetAsync");
+    // contiguous storage: the array is one vector of M N elements (Section 3.1)
+    if (lda == M || N == 1) return nrm_run_single_range(ctx, dtype, A, M * N, p, out, s, nullptr, 0, 0);
+    // otherwise: the norm of every column, then the norm of the N column norms
+    const size_t need = (size_t)N * (16 + es) + 512;
+    if (need > ctx->aux_bytes) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return set_cuda_err(ctx, e, "cudaStreamSynchronize");
+        if (ctx->aux) cudaFree(ctx->aux);
+        ctx->aux = nullptr;
+        ctx->aux_bytes = 0;
+        if (nrm_test_fail_alloc()) return NRM_ENOMEM;
+        e = cudaMalloc(&ctx->aux, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_cuda_err(ctx, e, "cudaMalloc(aux)");
+        }
+        ctx->aux_bytes = need;
+    }
+    int64_t *starts = (int64_t *)ctx->aux;
+    int64_t *lens = starts + N;
+    void *colnorm = (void *)(((uintptr_t)(lens + N) + 255) & ~(uintptr_t)255);
+    const unsigned blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 1024);
+    fill_columns_kernel<<<blocks, 256, 0, s>>>(starts, lens, N, M, lda);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_err(ctx, e, "fill_columns_kernel");
+    nrm_status st = nrm_batch_impl(ctx, dtype, A, (N - 1) * lda + M, starts, N, p, colnorm, nullptr, s, lens);
+    if (st != NRM_OK) return st;
+    return nrm_run_single_range(ctx, dtype, colnorm, N, p, out, s, nullptr, 0, 0);
 }
 
 // batch -----------------------------------------------------------------------
@@ -785,6 +857,7 @@ extern "C" nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, vo
     // the same tree as nrmf_d; only the cut depth is capped by the scratch size
     VecPlan pl{};
     pl.n = n;
+    pl.stride = 1;
     pl.m = (n + 63) / 64;
     pl.D = ceil_log2_i64(pl.m);
     int dw = std::max(pl.D - 7, ceil_log2_i64((int64_t)d->sms * NA_WPB * 2));

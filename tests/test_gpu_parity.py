@@ -524,3 +524,31 @@ def test_autotune_keeps_bits(nrm, dt):
         assert bits_equal(out.cpu().numpy(), oracle.nrm_batch(xb, off))
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_strided_parity(nrm, dt):
+    x = inputs.vector(300000, seed=21, vec=0, dtype=dt)
+    xd = dev(x)
+    for n, incx in ((300000, 1), (100000, 3), (99999, -3), (1000, -1), (5, 7), (1, -5), (60000, 5), (150000, -2)):
+        for p in (2.0, 3.0):
+            g = nrm.nrm_strided(xd, n, incx, p).item()
+            assert bits_equal(np.asarray(g, dt), oracle.nrm_strided(x, n, incx, p)), (n, incx, p)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_matrix_parity(nrm, dt):
+    x = inputs.vector(1 << 21, seed=22, vec=0, dtype=dt)
+    xd = dev(x)
+    for M, N, lda in ((1000, 200, 1000), (1000, 200, 1031), (64, 3000, 100), (1, 5000, 7), (70000, 3, 70001),
+                      (0, 5, 5), (5, 1, 9)):
+        for p in (2.0, 1.0, 3.0):
+            g = nrm.nrm_matrix(xd, M, N, lda, p).item()
+            assert bits_equal(np.asarray(g, dt), oracle.nrm_matrix(x, M, N, lda, p)), (M, N, lda, p)
+
+
+def test_complex_parity(nrm):
+    z = torch.complex(dev(inputs.vector(123457, seed=23, vec=0)), dev(inputs.vector(123457, seed=23, vec=1)))
+    g = nrm.nrmf_complex(z).item()
+    inter = torch.view_as_real(z).reshape(-1).cpu().numpy()
+    assert bits_equal(np.float64(g), oracle.nrm(inter))

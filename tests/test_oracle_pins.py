@@ -545,3 +545,44 @@ def test_pow_cutoff_p_prime(dt, cut):
     assert diff_below > 2000
     x = inputs.vector(5000, seed=12, vec=3, dtype=dt)
     assert oracle.nrm(x, cut) == oracle.nrm(x, math.inf) == np.max(np.abs(x))
+
+
+def test_strided_and_matrix_definitions():
+    """Section 3 (incx) and Section 3.1 (leading dimension): a strided vector
+    is its logical vector (incx < 0 taken backwards); a matrix with lda == M
+    is the one vector of M N elements; with lda > M the column norms are
+    combined by the same tree, and the result is accurate within the bound of
+    the two stacked trees against binary128 over all M N elements."""
+    x = rng_d(40, 100000)
+    assert same_bits(oracle.nrm_strided(x, 100000, 1), oracle.nrm(x))
+    assert same_bits(oracle.nrm_strided(x, 33333, 3), oracle.nrm(x[::3][:33333]))
+    assert same_bits(oracle.nrm_strided(x, 25000, -4), oracle.nrm(x[:100000:4][::-1][-25000:][:25000]))
+    assert same_bits(oracle.nrm_strided(x, 1000, -1), oracle.nrm(x[:1000][::-1]))
+    M, N, lda = 3000, 20, 3100
+    A = x[:N * lda]
+    cols = [A[j * lda:j * lda + M] for j in range(N)]
+    v = oracle.nrm_matrix(A, M, N, lda)
+    c = np.array([oracle.nrm(cc) for cc in cols])
+    assert same_bits(v, oracle.nrm(c))
+    allv = np.concatenate(cols)
+    hi, lo = oracle.ref_q128(allv)
+    depth = oracle.tree_depth(M, 64) + oracle.tree_depth(N, 64)
+    assert abs(float(v) - hi) / hi <= ub(depth) * EPS_D
+    assert same_bits(oracle.nrm_matrix(A, M, N, M), oracle.nrm(A[:M * N]))
+    for p in (1.0, 3.0, math.inf):
+        vp = oracle.nrm_matrix(A, M, N, lda, p)
+        hi, _ = oracle.ref_q128(allv, p)
+        assert abs(float(vp) - hi) / hi <= 1e-14
+
+
+def test_complex_as_reals():
+    """Section 1: |z|^2 = Re^2 + Im^2, so a complex array's Frobenius norm is
+    the norm of its interleaved real parts (accurate against the exact
+    sum of |z_i|^2)."""
+    re = rng_d(41, 5000)
+    im = rng_d(42, 5000)
+    inter = np.empty(10000)
+    inter[0::2], inter[1::2] = re, im
+    v = oracle.nrm(inter)
+    ex = mpmath.sqrt(sum(mpmath.mpf(float(a)) ** 2 + mpmath.mpf(float(b)) ** 2 for a, b in zip(re, im)))
+    assert rel(v, ex) <= ub(oracle.tree_depth(10000, 64)) * EPS_D
