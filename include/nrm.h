@@ -130,6 +130,16 @@ nrm_status nrmf_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *str
 nrm_status nrmf_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream);
 
 /*
+ * xNRMF as the paper recommends it (Section 3): the same vector recursion Z
+ * with v1_hypot, but the final reduction of the P lane partials uses the
+ * algorithm A -- R with the correctly rounded hypot RN(sqrt(x^2+y^2))
+ * (cr_hypot, Section 2), computed exactly with integer arithmetic -- instead
+ * of v1_hypot.  Arguments and errors as nrmf_*.
+ */
+nrm_status nrmf_za_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *stream);
+nrm_status nrmf_za_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream);
+
+/*
  * xNRMP (Section 4): *out = ||x[0..n)||_p by the same tree with the combine
  * chosen by p: p == 2 is exactly xNRMF; p == 1 sums |x| (Eq. vp1); p == +inf
  * takes max |x| (Eq. vpI); otherwise v1_lp (Listing 5, Eqs. sp and qp) with

@@ -44,6 +44,10 @@ def lib():
             "or_nrm_s": (f, [i64, vp, i32, f]),
             "or_nrm_batch_d": (None, [i64, vp, vp, i32, d, vp]),
             "or_nrm_batch_s": (None, [i64, vp, vp, i32, f, vp]),
+            "or_cr_hypot_d": (d, [d, d]),
+            "or_cr_hypot_s": (f, [f, f]),
+            "or_nrm_za_d": (d, [i64, vp, i32]),
+            "or_nrm_za_s": (f, [i64, vp, i32]),
             "or_nrm_strided_d": (d, [i64, vp, i64, i32, d]),
             "or_nrm_strided_s": (f, [i64, vp, i64, i32, f]),
             "or_nrm_matrix_d": (d, [i64, i64, i64, vp, i32, d]),
@@ -131,6 +135,22 @@ def nrm(x, p=2.0, P=None):
         return np.float64(lib().or_nrm_d(a.size, ptr, P or P_D, float(p)))
     a, ptr = _arr(x, np.float32)
     return np.float32(lib().or_nrm_s(a.size, ptr, P or P_S, float(np.float32(p))))
+
+
+def cr_hypot(x, y, dtype=np.float64):
+    """RN(sqrt(x^2 + y^2)): the correctly rounded hypot of the algorithm A."""
+    if np.dtype(dtype) == np.float64:
+        return np.float64(lib().or_cr_hypot_d(float(x), float(y)))
+    return np.float32(lib().or_cr_hypot_s(float(np.float32(x)), float(np.float32(y))))
+
+
+def nrm_za(x, P=None):
+    """Z with v1_hypot, then A (R with cr_hypot) over the lanes."""
+    if _is_d(x):
+        a, ptr = _arr(x, np.float64)
+        return np.float64(lib().or_nrm_za_d(a.size, ptr, P or P_D))
+    a, ptr = _arr(x, np.float32)
+    return np.float32(lib().or_nrm_za_s(a.size, ptr, P or P_S))
 
 
 def nrm_strided(buf, n, incx, p=2.0, P=None):

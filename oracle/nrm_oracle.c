@@ -27,6 +27,10 @@
  *   or_Z_*                 Z_x generalised to p lanes, Listing 4 (Section 3)
  *   or_nrm_*               xNRMF / xNRMP = Z then a final R over the lanes
  *                          (Section 3, recommendation for xNRMF)
+ *   or_cr_hypot_*          the correctly rounded hypot of the algorithm A
+ *                          (Section 2), from its definition with integers
+ *   or_nrm_za_*            Z then A for the final reduction (Section 3's
+ *                          recommendation for xNRMF)
  *   or_nrm_strided_*       a strided vector (BLAS incx, Section 3)
  *   or_nrm_matrix_*        a matrix with a leading dimension (Section 3.1)
  *   or_nrm_slot_*          the same tree evaluated in "slot form" (a perfect
@@ -67,6 +71,11 @@ typedef __float128 q128;
 /* combine operations                                                        */
 /* ------------------------------------------------------------------------ */
 
+static inline uint64_t bits_d(double x);
+static inline double from_bits_d(uint64_t u);
+static inline uint32_t bits_s(float x);
+static inline float from_bits_s(uint32_t u);
+
 /* Combine op selector: which per-node operation the tree applies. */
 enum { OP_HYPOT = 0, OP_LP = 1, OP_SUMABS = 2, OP_MAXABS = 3 };
 
@@ -99,6 +108,172 @@ OR_API float or_k1_s(float x, float y)
     const float S = fmaf(Q, Q, 1.0f);
     const float s = sqrtf(S);
     return M * s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* cr_hypot: the correctly rounded hypotenuse of the algorithm A (Section 2) */
+/* ------------------------------------------------------------------------ */
+
+typedef unsigned __int128 u128;
+
+/* floor(sqrt(N)) for N < 2^127: a binary64 estimate, then exact steps. */
+static uint64_t isqrt_u128(u128 N)
+{
+    double approx = (double)(uint64_t)(N >> 64) * 0x1p64 + (double)(uint64_t)N;
+    uint64_t g = (uint64_t)sqrt(approx);
+    while ((u128)g * g > N) --g;
+    while ((u128)(g + 1) * (g + 1) <= N) ++g;
+    return g;
+}
+
+/* 192-bit unsigned integers as hi * 2^128 + lo, for exact comparisons. */
+typedef struct { uint64_t hi; u128 lo; } u192;
+
+static u192 u192_shl(u128 v, int s) /* v * 2^s, 0 <= s <= 64 */
+{
+    u192 r;
+    if (s == 0) { r.hi = 0; r.lo = v; return r; }
+    r.hi = (uint64_t)(v >> (128 - s));
+    r.lo = v << s;
+    return r;
+}
+
+static u192 u192_add(u192 a, u192 b)
+{
+    u192 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo);
+    return r;
+}
+
+static int u192_cmp(u192 a, u192 b)
+{
+    if (a.hi != b.hi) return a.hi < b.hi ? -1 : 1;
+    if (a.lo != b.lo) return a.lo < b.lo ? -1 : 1;
+    return 0;
+}
+
+/* integer significand and exponent: v = sig * 2^e, sig in [2^52, 2^53)
+ * (subnormals normalised), v finite and nonzero */
+static void decompose_d(double v, uint64_t *sig, int *e)
+{
+    uint64_t b = bits_d(v) & 0x7fffffffffffffffull;
+    int ex = (int)(b >> 52);
+    uint64_t m = b & 0x000fffffffffffffull;
+    if (ex == 0) { /* subnormal: m * 2^-1074 */
+        int sh = 0;
+        while (!(m & (1ull << 52))) { m <<= 1; ++sh; }
+        *sig = m;
+        *e = -1074 - sh;
+    } else {
+        *sig = m | (1ull << 52);
+        *e = ex - 1075;
+    }
+}
+
+/*
+ * or_cr_hypot_d(x, y) = RN(sqrt(x^2 + y^2)) exactly (the cr_hypot the
+ * algorithm A uses; the paper takes it from CORE-MATH, which is not
+ * available here, so it is computed from its definition with integers):
+ *   X = max(|x|,|y|) = A 2^ex, Y = min = B 2^ey, d = ex - ey >= 0;
+ *   d >= 28: Y/X < 2^-27 and the exact value lies below X (1 + 2^-55), so
+ *   the result is X;
+ *   else S = A^2 4^d + B^2 (x^2 + y^2 = S 4^ey) and the result is
+ *   RN(sqrt(S / 4^d)) 2^ex, rounded to 53 bits by comparing 4S with the
+ *   squares of the midpoints (ties go to even);
+ *   both operands subnormal: RN(sqrt(a^2 + b^2)) 2^-1074 with a, b the
+ *   integer multiples of 2^-1074.
+ */
+OR_API double or_cr_hypot_d(double x, double y)
+{
+    double X = fabs(x), Y = fabs(y);
+    if (isinf(X) || isinf(Y)) return INFINITY;
+    if (isnan(X) || isnan(Y)) return x + y;
+    if (X < Y) { double t = X; X = Y; Y = t; }
+    if (Y == 0.0) return X;
+    if (X < 0x1p-1022) { /* both subnormal */
+        const u128 a = bits_d(X), b = bits_d(Y);
+        const u128 N = a * a + b * b;
+        uint64_t T = isqrt_u128(N);
+        const u128 m = (u128)(2 * T + 1) * (2 * T + 1); /* (2T+1)^2 vs 4N */
+        const u128 N4 = N << 2;
+        if (N4 > m || (N4 == m && (T & 1))) ++T;
+        return from_bits_d(T); /* T < 2^53: subnormal or the smallest binade */
+    }
+    uint64_t A, B;
+    int ex, ey;
+    decompose_d(X, &A, &ex);
+    decompose_d(Y, &B, &ey);
+    const int d = ex - ey;
+    if (d >= 28) return X;
+    const u128 A2 = (u128)A * A, B2 = (u128)B * B;
+    const u192 S = u192_add(u192_shl(A2, 2 * d), u192_shl(B2, 0));
+    const u192 S4 = u192_add(u192_shl(A2, 2 * d + 2), u192_shl(B2, 2));
+    const u128 Sd = A2 + (B2 >> (2 * d)); /* floor(S / 4^d) */
+    (void)S;
+    uint64_t T = isqrt_u128(Sd);
+    int e = ex;
+    int k = d; /* V = sqrt(S / 4^k) */
+    if (T >> 53) { /* V >= 2^53: round V / 2 instead */
+        T = isqrt_u128(Sd >> 2);
+        k = d + 1;
+        e = ex + 1;
+    }
+    const u128 m = (u128)(2 * T + 1) * (2 * T + 1);
+    const int c = u192_cmp(S4, u192_shl(m, 2 * k));
+    if (c > 0 || (c == 0 && (T & 1))) ++T;
+    if (T >> 53) { T >>= 1; e += 1; }
+    const int biased = e + 52 + 1023;
+    if (biased >= 2047) return INFINITY;
+    return from_bits_d(((uint64_t)biased << 52) | (T & 0x000fffffffffffffull));
+}
+
+/* binary32: the same with 24-bit significands; a gap of 14 or more gives X */
+OR_API float or_cr_hypot_s(float x, float y)
+{
+    float X = fabsf(x), Y = fabsf(y);
+    if (isinf(X) || isinf(Y)) return INFINITY;
+    if (isnan(X) || isnan(Y)) return x + y;
+    if (X < Y) { float t = X; X = Y; Y = t; }
+    if (Y == 0.0f) return X;
+    if (X < 0x1p-126f) {
+        const uint64_t a = bits_s(X), b = bits_s(Y);
+        const u128 N = (u128)a * a + (u128)b * b;
+        uint64_t T = isqrt_u128(N);
+        const u128 m = (u128)(2 * T + 1) * (2 * T + 1);
+        if ((N << 2) > m || ((N << 2) == m && (T & 1))) ++T;
+        return from_bits_s((uint32_t)T);
+    }
+    uint32_t bx = bits_s(X), by = bits_s(Y);
+    uint64_t A = (bx & 0x7fffff) | 0x800000, B;
+    int ex = (int)(bx >> 23) - 150, ey;
+    if ((by >> 23) == 0) {
+        B = by & 0x7fffff;
+        int sh = 0;
+        while (!(B & 0x800000)) { B <<= 1; ++sh; }
+        ey = -149 - sh;
+    } else {
+        B = (by & 0x7fffff) | 0x800000;
+        ey = (int)(by >> 23) - 150;
+    }
+    const int d = ex - ey;
+    if (d >= 14) return X;
+    const u128 A2 = (u128)A * A, B2 = (u128)B * B;
+    const u128 S4 = ((A2 << (2 * d)) + B2) << 2;
+    const u128 Sd = A2 + (B2 >> (2 * d));
+    uint64_t T = isqrt_u128(Sd);
+    int e = ex, k = d;
+    if (T >> 24) {
+        T = isqrt_u128(Sd >> 2);
+        k = d + 1;
+        e = ex + 1;
+    }
+    const u128 m = ((u128)(2 * T + 1) * (2 * T + 1)) << (2 * k);
+    if (S4 > m || (S4 == m && (T & 1))) ++T;
+    if (T >> 24) { T >>= 1; e += 1; }
+    const int biased = e + 23 + 127;
+    if (biased >= 255) return INFINITY;
+    return from_bits_s(((uint32_t)biased << 23) | (uint32_t)(T & 0x7fffff));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -582,6 +757,47 @@ OR_API float or_nrm_s(int64_t n, const float *x, int P, float p)
     float *f = (float *)malloc(sizeof(float) * (size_t)P);
     Z_s(n, x, P, &c, f);
     const float v = R_s(P, f, &c);
+    free(f);
+    return v;
+}
+
+/* The paper's recommended xNRMF (Section 3): Z with v1_hypot on the vector
+ * rows, then the final reduction of the P lane partials by A, i.e. R with
+ * the correctly rounded hypot. */
+static double R_cr_d(int64_t n, const double *x)
+{
+    if (n == 1) return fabs(x[0]);
+    if (n == 2) return or_cr_hypot_d(x[0], x[1]);
+    const int64_t p = (n >> 1) + (n & 1);
+    return or_cr_hypot_d(R_cr_d(p, x), R_cr_d(n - p, x + p));
+}
+
+static float R_cr_s(int64_t n, const float *x)
+{
+    if (n == 1) return fabsf(x[0]);
+    if (n == 2) return or_cr_hypot_s(x[0], x[1]);
+    const int64_t p = (n >> 1) + (n & 1);
+    return or_cr_hypot_s(R_cr_s(p, x), R_cr_s(n - p, x + p));
+}
+
+OR_API double or_nrm_za_d(int64_t n, const double *x, int P)
+{
+    if (n <= 0) return 0.0;
+    comb_d c = comb_for_d(2.0);
+    double *f = (double *)malloc(sizeof(double) * (size_t)P);
+    Z_d(n, x, P, &c, f);
+    const double v = R_cr_d(P, f);
+    free(f);
+    return v;
+}
+
+OR_API float or_nrm_za_s(int64_t n, const float *x, int P)
+{
+    if (n <= 0) return 0.0f;
+    comb_s c = comb_for_s(2.0f);
+    float *f = (float *)malloc(sizeof(float) * (size_t)P);
+    Z_s(n, x, P, &c, f);
+    const float v = R_cr_s(P, f);
     free(f);
     return v;
 }

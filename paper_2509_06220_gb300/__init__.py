@@ -91,6 +91,8 @@ def load():
         "nrmf_s": (st, [vp, vp, i64, vp, vp]),
         "nrmf_d": (st, [vp, vp, i64, vp, vp]),
         "nrmp_s": (st, [vp, vp, i64, ctypes.c_float, vp, vp]),
+        "nrmf_za_s": (st, [vp, vp, i64, vp, vp]),
+        "nrmf_za_d": (st, [vp, vp, i64, vp, vp]),
         "nrmp_d": (st, [vp, vp, i64, ctypes.c_double, vp, vp]),
         "nrm_batch": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, vp]),
         "nrm_batch_graph": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, ctypes.POINTER(vp)]),
@@ -277,6 +279,21 @@ def nrmp(x, p=2.0, out=None, stream=None, ctx=None):
 def nrmf(x, out=None, stream=None, ctx=None):
     """xNRMF: the Frobenius norm by the recursive v1_hypot tree."""
     return nrmp(x, 2.0, out, stream, ctx)
+
+
+def nrmf_za(x, out=None, stream=None, ctx=None):
+    """xNRMF with the algorithm A (correctly rounded hypot) for the final
+    reduction of the lane partials: the paper's recommended pairing."""
+    import torch
+    _check_vec(x)
+    dt = _dtype_code(x)
+    c = ctx or context(x.device)
+    if out is None:
+        out = torch.empty((), dtype=x.dtype, device=x.device)
+    f = load().nrmf_za_d if dt == NRM_F64 else load().nrmf_za_s
+    c.check(f(c.h, ctypes.c_void_p(x.data_ptr() if x.numel() else 0), x.numel(), ctypes.c_void_p(out.data_ptr()),
+              _stream(stream)), "nrmf_za")
+    return out
 
 
 def nrm_batch(x, offsets, p=2.0, out=None, status=None, stream=None, ctx=None):

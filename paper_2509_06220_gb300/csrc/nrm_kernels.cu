@@ -98,7 +98,9 @@ __device__ __forceinline__ void load_slot(const T *src, T (&r)[Geo<T>::V]) {
 // The register cap comes from the combine (Op::kMaxRegs): the trees are
 // latency-bound, so more resident warps pay more than per-thread ILP (a
 // sweep on GB300 found 64 registers best for v1_hypot in both precisions).
-template <typename T, int G, class Op>
+// FinalA: reduce the P lane partials with the correctly rounded hypot (the
+// algorithm A; Z with A is the paper's recommended xNRMF) instead of op.
+template <typename T, int G, class Op, bool FinalA = false>
 __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
     constexpr int V = Geo<T>::V;
     constexpr int P = Geo<T>::P;
@@ -172,7 +174,9 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
             h >>= 1;
         }
         if (root) {
-            const T res = lane_reduce<T, Op>(r, op, lane);
+            T res;
+            if constexpr (FinalA) res = lane_reduce<T, OpCrHypot<T>>(r, OpCrHypot<T>{}, lane);
+            else res = lane_reduce<T, Op>(r, op, lane);
             if (lane == 0) a.out[v] = res;
         }
         if (batch) {
@@ -511,7 +515,7 @@ template <typename T> static const nrm_tuning &tune_of(const nrm_ctx *c) {
     return c->tune[sizeof(T) == 8 ? NRM_F64 : NRM_F32];
 }
 
-template <typename T, class Op>
+template <typename T, class Op, bool FinalA = false>
 static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, int64_t grid_warps,
                                cudaStream_t s) {
     const nrm_tuning &tu = tune_of<T>(c);
@@ -523,11 +527,12 @@ static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, i
     switch (tu.group_log2) {
 #define NRM_LAUNCH_G(GG)                                                                                    \
     case GG: {                                                                                              \
-        cudaFuncSetAttribute(tree_kernel<T, GG, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<T, GG, Op>, wpb * 32, smem);       \
+        cudaFuncSetAttribute(tree_kernel<T, GG, Op, FinalA>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                             (int)smem);                                                                    \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<T, GG, Op, FinalA>, wpb * 32, smem); \
         occ = std::max(1, std::min(occ, tu.blocks_per_sm));                                                \
         blocks = std::max<int64_t>(1, std::min<int64_t>((grid_warps + wpb - 1) / wpb, (int64_t)c->sms * occ)); \
-        tree_kernel<T, GG, Op><<<(unsigned)blocks, wpb * 32, smem, s>>>(a, op);                             \
+        tree_kernel<T, GG, Op, FinalA><<<(unsigned)blocks, wpb * 32, smem, s>>>(a, op);                     \
         e = cudaGetLastError();                                                                             \
         break;                                                                                              \
     }
@@ -558,7 +563,7 @@ template <typename T, class F> static cudaError_t with_op(T p, F &&f) {
 
 template <typename T>
 static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cudaStream_t s, int64_t item_lo,
-                             int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1) {
+                             int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1, bool final_a = false) {
     VecPlan pl;
     if (plan_in) pl = *plan_in;
     else if (!plan_single(c, n, P_of<T>(), pl)) return NRM_EINVAL;
@@ -581,7 +586,9 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
     a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>((char *)c->ws + L.slots);
     const int64_t warps = a.item_hi - a.item_lo;
-    cudaError_t e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, warps, s); });
+    cudaError_t e;
+    if (final_a) e = launch_tree<T, OpHypot<T>, true>(c, a, OpHypot<T>{}, warps, s);
+    else e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, warps, s); });
     return set_cuda_err(c, e, "tree_kernel launch");
 }
 
@@ -616,6 +623,22 @@ extern "C" nrm_status nrmf_s(nrm_ctx *ctx, const float *x, int64_t n, float *out
 extern "C" nrm_status nrmf_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream) {
     return nrm_entry<double>(ctx, x, n, 2.0, out, stream);
 }
+// Z with A for the final reduction (Section 3's recommended xNRMF)
+template <typename T> static nrm_status za_entry(nrm_ctx *c, const T *x, int64_t n, T *out, void *stream) {
+    nrm_status st = check_args<T>(c, x, n, T(2), out);
+    if (st != NRM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return set_cuda_err(c, cudaMemsetAsync(out, 0, sizeof(T), s), "cudaMemsetAsync");
+    return run_single<T>(c, x, n, T(2), out, s, 0, 0, nullptr, 1, true);
+}
+
+extern "C" nrm_status nrmf_za_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *stream) {
+    return za_entry<float>(ctx, x, n, out, stream);
+}
+extern "C" nrm_status nrmf_za_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream) {
+    return za_entry<double>(ctx, x, n, out, stream);
+}
+
 extern "C" nrm_status nrmp_s(nrm_ctx *ctx, const float *x, int64_t n, float p, float *out, void *stream) {
     return nrm_entry<float>(ctx, x, n, p, out, stream);
 }

@@ -552,3 +552,38 @@ def test_complex_parity(nrm):
     g = nrm.nrmf_complex(z).item()
     inter = torch.view_as_real(z).reshape(-1).cpu().numpy()
     assert bits_equal(np.float64(g), oracle.nrm(inter))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_za_parity(nrm, dt):
+    """Z with A for the final reduction (the paper's recommended xNRMF):
+    bitwise against the oracle over many sizes and offsets; two-element
+    vectors give cr_hypot(x0, x1) itself (random gaps around the shortcut,
+    exact triples, subnormals)."""
+    x = inputs.vector(600000, seed=24, vec=0, dtype=dt)
+    xd = dev(x)
+    for n, s in ((1, 0), (2, 0), (63, 1), (64, 0), (129, 3), (1000, 0), (65537, 5), (300000, 7), (599990, 1)):
+        g = nrm.nrmf_za(xd[s:s + n]).item()
+        assert bits_equal(np.asarray(g, dt), oracle.nrm_za(x[s:s + n])), (n, s)
+    r = random.Random(25)
+    thr = 28 if dt == np.float64 else 14
+    small = -1070 if dt == np.float64 else -148
+    pairs = []
+    for _ in range(1500):
+        e = r.randint(small, 100)
+        g = r.choice([0, 1, thr - 1, thr, thr + 1, r.randint(0, 2 * thr)])
+        pairs.append(((1 + r.random()) * 2.0 ** e, -(1 + r.random()) * 2.0 ** (e - g)))
+    for _ in range(500):
+        m, k = r.randint(1, 2 ** 11), r.randint(1, 2 ** 11)
+        pairs.append((float(m * m - k * k), float(2 * m * k)))
+    tiny = float(np.finfo(dt).smallest_subnormal)
+    pairs += [(tiny, tiny), (3 * tiny, 4 * tiny), (float(np.finfo(dt).tiny), tiny), (float(np.finfo(dt).max), 1.0)]
+    arr = np.array(pairs, dtype=dt).reshape(-1)
+    ad = dev(arr)
+    out = torch.empty(len(pairs), dtype=TD[dt], device=DEV)
+    for i in range(len(pairs)):
+        nrm.nrmf_za(ad[2 * i:2 * i + 2], out=out[i])
+    o = out.cpu().numpy()
+    for i, (a, b) in enumerate(pairs):
+        want = oracle.cr_hypot(dt(a), dt(b), dt)
+        assert bits_equal(o[i], np.asarray(want, dt)), (a, b, o[i], want)

@@ -586,3 +586,84 @@ def test_complex_as_reals():
     v = oracle.nrm(inter)
     ex = mpmath.sqrt(sum(mpmath.mpf(float(a)) ** 2 + mpmath.mpf(float(b)) ** 2 for a, b in zip(re, im)))
     assert rel(v, ex) <= ub(oracle.tree_depth(10000, 64)) * EPS_D
+
+
+def _exact_rn_hypot(x, y, dt):
+    """RN(sqrt(x^2 + y^2)) in format dt, decided exactly: candidates from a
+    high-precision estimate, then exact rational comparisons with the
+    midpoints (ties to even)."""
+    from fractions import Fraction
+    S = Fraction(float(x)) ** 2 + Fraction(float(y)) ** 2
+    est = mpmath.sqrt(mpmath.mpf(float(x)) ** 2 + mpmath.mpf(float(y)) ** 2)
+    c = dt(float(est))
+    if not np.isfinite(c):
+        return c
+    cands = sorted({c, np.nextafter(c, dt(np.inf)), np.nextafter(c, dt(0)),
+                    np.nextafter(np.nextafter(c, dt(0)), dt(0))}, key=float)
+    best = None
+    for v in cands:
+        lo = Fraction(float(np.nextafter(v, dt(0)))) if v > 0 else Fraction(0)
+        hi = Fraction(float(np.nextafter(v, dt(np.inf))))
+        mlo, mhi = (lo + Fraction(float(v))) / 2, (hi + Fraction(float(v))) / 2
+        below = mlo * mlo < S or (mlo * mlo == S and int(np.asarray(v).view(np.uint64 if dt == np.float64 else np.uint32)) % 2 == 0)
+        above = S < mhi * mhi or (S == mhi * mhi and int(np.asarray(v).view(np.uint64 if dt == np.float64 else np.uint32)) % 2 == 0)
+        if below and above:
+            best = v
+    return best
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_cr_hypot_is_correctly_rounded(dt):
+    """Section 2: A uses a correctly rounded hypot (|eps_h| <= eps).  The
+    oracle's cr_hypot equals RN(sqrt(x^2 + y^2)) decided exactly, on random
+    pairs with every exponent gap around the shortcut threshold, subnormals,
+    exact Pythagorean triples (3-4-5 scaled) and near-ties."""
+    r = random.Random(17)
+    big = 1000 if dt == np.float64 else 120
+    small = -1070 if dt == np.float64 else -148
+    thr = 28 if dt == np.float64 else 14
+    cases = [(3.0, 4.0), (5.0, 12.0), (1.0, 1.0), (0.0, 2.5), (np.finfo(dt).tiny, np.finfo(dt).tiny),
+             (np.finfo(dt).smallest_subnormal, np.finfo(dt).smallest_subnormal)]
+    for _ in range(3000):
+        e = r.randint(small, big)
+        g = r.choice([0, 0, 1, 2, thr - 2, thr - 1, thr, thr + 1, r.randint(0, 2 * thr)])
+        cases.append(((1 + r.random()) * 2.0 ** e, (1 + r.random()) * 2.0 ** (e - g)))
+    for _ in range(300):
+        m, n = r.randint(1, 2 ** 11), r.randint(1, 2 ** 11)
+        k = r.randint(-40, 40)
+        cases.append(((m * m - n * n) * 2.0 ** k, (2 * m * n) * 2.0 ** k))
+    checked = 0
+    for a, b in cases:
+        a, b = dt(a), dt(b)
+        if not (np.isfinite(a) and np.isfinite(b)):
+            continue
+        want = _exact_rn_hypot(a, b, dt)
+        if want is None:
+            continue
+        got = oracle.cr_hypot(a, b, dt)
+        assert same_bits(np.asarray(got, dt), np.asarray(want, dt)), (a, b, got, want)
+        checked += 1
+    assert checked > 3000
+    assert oracle.cr_hypot(3.0, 4.0, dt) == 5.0
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_za_variant(dt):
+    """Section 3's recommendation: Z with A for the final reduction.  It is
+    accurate within Theorem 3's bound with the v1_hypot factor (Eq. reH) on
+    the vector-row levels and eps' = eps on the lane levels, and equals the
+    H form when only one lane is nonzero."""
+    P = oracle.P_D if dt == np.float64 else oracle.P_S
+    eps = EPS_D if dt == np.float64 else EPS_S
+    prec = "D" if dt == np.float64 else "S"
+    x = inputs.vector(1 << 18, seed=50, vec=0, dtype=dt)
+    v = oracle.nrm_za(x)
+    hi, lo = oracle.ref_q128(x)
+    rows = oracle.tree_depth(x.size, P) - int(math.log2(P))
+    (_, _), (uh, ul) = oracle.reH_factors(prec)
+    bound = ((mpmath.mpf(uh) + ul) ** rows * (1 + mpmath.mpf(eps)) ** int(math.log2(P)) - 1)
+    assert abs(float(v) - hi) / hi <= float(bound)
+    one = np.zeros(5 * P, dtype=dt)
+    one[7] = dt(-2.5)
+    assert oracle.nrm_za(one) == oracle.nrm(one) == dt(2.5)
+    assert oracle.nrm_za(np.zeros(0, dt)) == 0.0
