@@ -354,6 +354,22 @@ void nrm_test_inject_alloc_failures(int count);
 nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad, double *example,
                                 void *stream);
 
+/* Test hook: evaluate the library's pow (the pow of Listing 5, Section 4)
+ * elementwise, out[i] = pow(x[i], y[i]), with the same device code the
+ * xNRMP tree kernels use; x, y and out are device arrays of n elements of
+ * `dtype` (NRM_F64: the fixed-point integer pow, NRM_F32: the binary32
+ * double-word pow).  Asynchronous on `stream`; NRM_EINVAL for n < 0, null
+ * arrays or an unknown dtype. */
+nrm_status nrm_test_pow(nrm_dtype dtype, const void *x, const void *y, void *out, int64_t n, void *stream);
+
+/* Test hook: v1_lp (Listing 5, Section 4's Eq. sp) elementwise with
+ * h = p/2 and ip = 1/p rounded in `dtype`, out[i] = v1_lp(x[i], y[i]),
+ * exactly as the xNRMP tree kernels combine (for binary64 the integer
+ * quotient and pow, with the FP64 form for inf, NaN and subnormal
+ * operands).  Device arrays of n elements; asynchronous on `stream`;
+ * NRM_EINVAL for n < 0, null arrays, p <= 0 or NaN, or an unknown dtype. */
+nrm_status nrm_test_lp(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n, void *stream);
+
 /* Test hook: copy the first `count` ticket counters of the context's
  * workspace to host memory (synchronous).  Between calls they are all zero. */
 nrm_status nrm_test_read_tickets(const nrm_ctx *ctx, uint32_t *host, int64_t count);

@@ -35,6 +35,10 @@ def lib():
             "or_pow_s": (f, [f, f]),
             "or_lp_d": (d, [d, d, d, d]),
             "or_lp_s": (f, [f, f, f, f]),
+            "or_pow_arr_d": (None, [i64, vp, vp, vp]),
+            "or_pow_arr_s": (None, [i64, vp, vp, vp]),
+            "or_lp_arr_d": (None, [i64, d, d, vp, vp, vp]),
+            "or_lp_arr_s": (None, [i64, f, f, vp, vp, vp]),
             "or_R_d": (d, [i64, vp, d]),
             "or_R_s": (f, [i64, vp, f]),
             "or_R_trace": (i64, [i64, vp]),
@@ -87,6 +91,32 @@ def pow_(x, y, dtype=np.float64):
     if np.dtype(dtype) == np.float64:
         return np.float64(lib().or_pow_d(float(x), float(y)))
     return np.float32(lib().or_pow_s(float(np.float32(x)), float(np.float32(y))))
+
+
+def pow_arr(x, y):
+    """Elementwise pow over two arrays of one dtype (float64 or float32)."""
+    dt = np.asarray(x).dtype
+    xa, xp = _arr(x, dt)
+    ya, yp = _arr(y, dt)
+    out = np.empty(xa.shape, dt)
+    f = lib().or_pow_arr_d if dt == np.float64 else lib().or_pow_arr_s
+    f(xa.size, xp, yp, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def lp_arr(p, x, y):
+    """Elementwise v1_lp over two arrays, h = p*0.5 and ip = 1/p in their dtype."""
+    dt = np.asarray(x).dtype
+    xa, xp = _arr(x, dt)
+    ya, yp = _arr(y, dt)
+    out = np.empty(xa.shape, dt)
+    if dt == np.float64:
+        lib().or_lp_arr_d(xa.size, float(p) * 0.5, 1.0 / float(p), xp, yp, out.ctypes.data_as(ctypes.c_void_p))
+    else:
+        p32 = np.float32(p)
+        lib().or_lp_arr_s(xa.size, float(np.float32(p32 * np.float32(0.5))), float(np.float32(np.float32(1) / p32)),
+                          xp, yp, out.ctypes.data_as(ctypes.c_void_p))
+    return out
 
 
 def lp(p, x, y, dtype=np.float64):

@@ -22,7 +22,9 @@
  *                          choice open); written here from the textbook
  *                          identities x^y = 2^(y log2 x), ln f = 2 atanh(s),
  *                          s = (f-1)/(f+1), and the Taylor series of atanh
- *                          and exp, with double-word (Dekker) arithmetic.
+ *                          and exp: binary64 in exact fixed-point integer
+ *                          arithmetic, binary32 with double-word (Dekker)
+ *                          arithmetic.
  *   or_R_*                 R_x, Listing 1 / Eq. r (Section 2)
  *   or_Z_*                 Z_x generalised to p lanes, Listing 4 (Section 3)
  *   or_nrm_*               xNRMF / xNRMP = Z then a final R over the lanes
@@ -79,6 +81,16 @@ static inline float from_bits_s(uint32_t u);
 /* Combine op selector: which per-node operation the tree applies. */
 enum { OP_HYPOT = 0, OP_LP = 1, OP_SUMABS = 2, OP_MAXABS = 3 };
 
+/* fmin / fmax of Listings 2 and 5 with C's Annex F rule written out: a NaN
+ * argument counts as missing data and the other one is returned.  The rule
+ * is applied to signalling NaNs too (some libms return a NaN for those,
+ * e.g. one built on AArch64's FMINNM), so that the result does not depend
+ * on the host's libm. */
+static double min_d(double a, double b) { return isnan(a) ? b : isnan(b) ? a : (b < a ? b : a); }
+static double max_d(double a, double b) { return isnan(a) ? b : isnan(b) ? a : (b > a ? b : a); }
+static float min_s(float a, float b) { return isnan(a) ? b : isnan(b) ? a : (b < a ? b : a); }
+static float max_s(float a, float b) { return isnan(a) ? b : isnan(b) ? a : (b > a ? b : a); }
+
 /* v1_hypot (Listing 2, Section 2): every statement is one IEEE operation.
  * fmin/fmax return the other operand when one is a NaN, so Q is never a NaN
  * (this also makes K(a,0)=a and K(0,0)=0 exact). */
@@ -86,10 +98,10 @@ OR_API double or_k1_d(double x, double y)
 {
     const double X = fabs(x);
     const double Y = fabs(y);
-    const double m = fmin(X, Y);
-    const double M = fmax(X, Y);
+    const double m = min_d(X, Y);
+    const double M = max_d(X, Y);
     const double q = m / M;
-    const double Q = fmax(q, 0.0);
+    const double Q = max_d(q, 0.0);
     const double S = fma(Q, Q, 1.0);
     const double s = sqrt(S);
     return M * s;
@@ -101,10 +113,10 @@ OR_API float or_k1_s(float x, float y)
 {
     const float X = fabsf(x);
     const float Y = fabsf(y);
-    const float m = fminf(X, Y);
-    const float M = fmaxf(X, Y);
+    const float m = min_s(X, Y);
+    const float M = max_s(X, Y);
     const float q = m / M;
-    const float Q = fmaxf(q, 0.0f);
+    const float Q = max_s(q, 0.0f);
     const float S = fmaf(Q, Q, 1.0f);
     const float s = sqrtf(S);
     return M * s;
@@ -285,25 +297,15 @@ static inline double from_bits_d(uint64_t u) { double x; memcpy(&x, &u, 8); retu
 static inline uint32_t bits_s(float x) { uint32_t u; memcpy(&u, &x, 4); return u; }
 static inline float from_bits_s(uint32_t u) { float x; memcpy(&x, &u, 4); return x; }
 
-/* 2^k as a double for -1074 <= k <= 1023, built from its bit pattern. */
-static double pow2_d(int k)
-{
-    if (k >= -1022) return from_bits_d((uint64_t)(k + 1023) << 52);
-    return from_bits_d(1ull << (k + 1074));
-}
-
+/* 2^k as a binary32 for -149 <= k <= 127, built from its bit pattern. */
 static float pow2_s(int k)
 {
     if (k >= -126) return from_bits_s((uint32_t)(k + 127) << 23);
     return from_bits_s(1u << (k + 149));
 }
 
-/* ln 2 and 1/ln 2 as double-word constants (hi = RN(c), lo = RN(c - hi)). */
-#define LN2_HI 0x1.62e42fefa39efp-1
-#define LN2_LO 0x1.abc9e3b39803fp-56
-#define ILN2_HI 0x1.71547652b82fep+0
-#define ILN2_LO 0x1.777d0ffda0d24p-56
-#define SQRT2_D 0x1.6a09e667f3bcdp+0
+/* ln 2 and 1/ln 2 as binary32 double-word constants (hi = RN(c),
+ * lo ~ c - hi), for the binary32 pow. */
 #define LN2F_HI 0x1.62e430p-1f
 #define LN2F_LO -0x1.05c610p-29f
 #define ILN2F_HI 0x1.715476p+0f
@@ -311,114 +313,172 @@ static float pow2_s(int k)
 #define SQRT2_S 0x1.6a09e6p+0f
 
 /*
- * or_pow_d(x, y) ~ x^y for x >= 0 and finite y > 0: the pow of Listing 5.
+ * or_pow_d(x, y) ~ x^y for x >= 0 and y > 0: the binary64 pow of Listing 5.
  * The paper leaves the pow to the platform (cr_pow, __builtin_pow, SLEEF);
- * this one is defined here so that the oracle and the GPU compute the same
- * bits.  Steps:
- *  1. x = 2^e f with f in [sqrt(1/2), sqrt(2)).
- *  2. s = (f-1)/(f+1) as a double-word s_hi + s_lo (f-1 and the rounding
- *     error of f+1 are exact; the quotient is corrected by its exact FMA
- *     remainder).
- *  3. ln f = 2 atanh(s) = 2s + 2s z T(z), z = s^2, T(z) = sum_{j>=0}
- *     z^j/(2j+3) truncated after 12 terms (|s| <= 0.1716, so the next term
- *     is below 2^-62 relative).
- *  4. log2 x = e + ln f / ln 2 and t = y log2 x, both double-word.
- *  5. t = k + r with k = rint(t), |r| <= 1/2; 2^r = exp(r ln 2) by its
- *     Taylor series to degree 14 (|r ln 2| <= 0.347), and 2^t = 2^k 2^r.
- * Exact cases: pow(0,y) = 0, pow(1,y) = 1, pow(inf,y) = inf.
+ * this one is defined here in fixed-point integer arithmetic from start to
+ * end, so that the oracle and the GPU compute the same bits and the pow
+ * needs no FP64 operation.  A "Qk" integer v stands for v 2^-k; every right
+ * shift is a floor.  Steps:
+ *  1. x = M 2^(E-52) with M in [2^52, 2^53); if M >= THR = ceil(sqrt2 2^52)
+ *     then f = M/2^53 and E += 1, else f = M/2^52 (f in [1/sqrt2, sqrt2)).
+ *  2. s = (f-1)/(f+1) = num/den with num = M - 2^k and den = M + 2^k exact
+ *     (2^k the divisor of step 1).  |s| = Qs 2^es with Qs the 128-bit floor
+ *     quotient floor(An 2^128 / Dn) of An = |num| 2^la and Dn = den 2^ld,
+ *     both normalised to [2^63, 2^64) (An halved first when not below Dn).
+ *  3. atanh(s) = s W, W = 1 + z T(z), z = s^2, T(z) = sum_{j=0}^{10}
+ *     z^j/(2j+3): z in Q69 from the top word of Qs, T by Horner in Q65 with
+ *     coefficients floor(2^65/(2j+3)), w = z T in Q70 (|s| <= 0.1716, the
+ *     first omitted term z^12/25 is below 2^-65).
+ *  4. log2 f = 2 atanh(s)/ln 2 = s W K with K = 2/ln 2 rounded to Q126:
+ *     V = Qs/2 + floor(Qs/2 w) (129 bits never needed), Gm = the top 128
+ *     bits of V K (the three high partial products).
+ *  5. log2 x = E + log2 f: for E != 0 a Q116 fixed-point sum (|E| <= 1075,
+ *     |log2 f| <= 1/2); for E = 0 the 128-bit Gm with its exponent.
+ *  6. t = y log2 x: y's 53-bit significand times the 128-bit log2 x exactly
+ *     (192 bits), then truncated to Q64; |t| >= 2^11 overflows (log2 x > 0)
+ *     or underflows (log2 x < 0).
+ *  7. t = k + r with k = floor(t + 1/2) and r in [-1/2, 1/2) in Q64;
+ *     u = r ln 2 in Q64 (ln 2 rounded to Q63); e^u by its Taylor series to
+ *     degree 15, Horner in Q62 with coefficients floor(2^62/j!)
+ *     (|u| <= 0.347, the first omitted term is below 2^-68).
+ *  8. x^y = e^u 2^k rounded to nearest (ties to even) to 53 bits, or to a
+ *     multiple of 2^-1074 below 2^-1022; above 2^1024 it is +inf.
+ * Exact cases: pow(0,y) = 0, pow(1,y) = 1, pow(inf,y) = inf, pow(x,0) = 1,
+ * pow(x,inf) = 0 (x < 1) or inf (x > 1), and pow(2^a, b) = 2^(ab) whenever
+ * ab is an integer (then r = 0 and e^u = 1 exactly).
  */
+#define POW_THR 0x16a09e667f3bcdull /* ceil(sqrt(2) 2^52) */
+#define K126_HI 0xb8aa3b295c17f0bbull /* RN(2/ln2 2^126), high word */
+#define K126_LO 0xbe87fed0691d3e89ull /* low word */
+#define LN2_Q63 0x58b90bfbe8e7bcd6ull /* RN(ln2 2^63) */
+
+typedef __int128 i128;
+
+static int clz64(uint64_t v) { return v ? __builtin_clzll(v) : 64; }
+
+/* floor(v / 2^s) of a 192-bit value (hi 2^128 + lo), 0 <= s */
+static u128 u192_shr(u192 v, int s)
+{
+    if (s >= 192) return 0;
+    if (s >= 128) return (u128)(v.hi >> (s - 128));
+    if (s == 0) return v.lo;
+    return (v.lo >> s) | ((u128)v.hi << (128 - s));
+}
+
 OR_API double or_pow_d(double x, double y)
 {
     if (isnan(x) || isnan(y)) return x + y;
     if (x == 0.0) return 0.0;
     if (x == 1.0) return 1.0;
     if (isinf(x)) return x;
+    if (y == 0.0) return 1.0;
+    if (isinf(y)) return x < 1.0 ? 0.0 : INFINITY;
     /* step 1 */
-    uint64_t b = bits_d(x);
-    int e = 0;
-    if ((b >> 52) == 0) { /* subnormal: scale by 2^54 (exact) */
-        x = x * 0x1p54;
-        b = bits_d(x);
-        e = -54;
+    uint64_t M;
+    int E;
+    decompose_d(x, &M, &E);
+    E += 52;
+    int k = 52;
+    if (M >= POW_THR) { k = 53; E += 1; }
+    /* steps 2-5: log2 x = (neg ? -1 : 1) Lm 2^eL */
+    const int64_t num = (int64_t)M - (int64_t)(1ull << k);
+    const uint64_t den = M + (1ull << k);
+    u128 Lm;
+    int eL;
+    int neg;
+    if (num == 0) {
+        neg = E < 0;
+        Lm = (u128)(uint64_t)(E < 0 ? -E : E) << 116;
+        eL = -116;
+    } else {
+        neg = num < 0;
+        const uint64_t A = (uint64_t)(num < 0 ? -num : num);
+        const int la = clz64(A), ld = clz64(den);
+        uint64_t An = A << la;
+        const uint64_t Dn = den << ld;
+        int es = -128 + ld - la;
+        if (An >= Dn) { An >>= 1; es += 1; }
+        /* step 2: Qs = floor(An 2^128 / Dn) in two 64-bit digits */
+        const u128 N1 = (u128)An << 64;
+        const uint64_t q1 = (uint64_t)(N1 / Dn);
+        const uint64_t r1 = (uint64_t)(N1 % Dn);
+        const uint64_t q0 = (uint64_t)(((u128)r1 << 64) / Dn);
+        const u128 Qs = ((u128)q1 << 64) | q0;
+        const int sig = -(es + 128); /* |s| in [2^-(sig+1), 2^-sig) */
+        /* step 3 */
+        const u128 P = (u128)q1 * q1;
+        const int zs = 59 + 2 * sig;
+        const uint64_t z69 = zs < 128 ? (uint64_t)(P >> zs) : 0;
+        u128 T = ((u128)1 << 65) / 23;
+        for (int j = 9; j >= 0; --j)
+            T = ((u128)1 << 65) / (uint64_t)(2 * j + 3) + ((T * z69) >> 69);
+        const uint64_t w70 = (uint64_t)((T * z69) >> 64);
+        /* step 4 */
+        const u128 Qh = Qs >> 1;
+        const u128 V = Qh + ((((u128)(uint64_t)(Qh >> 64) * w70) + (((u128)(uint64_t)Qh * w70) >> 64)) >> 6);
+        const uint64_t Vh = (uint64_t)(V >> 64), Vl = (uint64_t)V;
+        const u128 Gm = (u128)Vh * K126_HI + (((u128)Vh * K126_LO) >> 64) + (((u128)Vl * K126_HI) >> 64);
+        const int eG = es + 3;
+        /* step 5 */
+        if (E == 0) {
+            Lm = Gm;
+            eL = eG;
+        } else {
+            const int sh = -(eG + 116);
+            const u128 g = sh < 128 ? Gm >> sh : 0;
+            const u128 base = (u128)(uint64_t)(E < 0 ? -E : E) << 116;
+            Lm = ((E < 0) == neg) ? base + g : base - g;
+            eL = -116;
+            neg = E < 0;
+        }
     }
-    e += (int)(b >> 52) - 1023;
-    double f = from_bits_d((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull);
-    if (f > SQRT2_D) { f = f * 0.5; e = e + 1; }
-    /* step 2 */
-    const double a = f - 1.0;
-    const double d_hi = f + 1.0;
-    const double d_lo = f - (d_hi - 1.0);
-    const double s_hi = a / d_hi;
-    double rr = fma(-s_hi, d_hi, a);
-    rr = fma(-s_hi, d_lo, rr);
-    const double s_lo = rr / d_hi;
-    /* step 3 */
-    const double z = s_hi * s_hi;
-    double T = 1.0 / 25.0;
-    T = fma(T, z, 1.0 / 23.0);
-    T = fma(T, z, 1.0 / 21.0);
-    T = fma(T, z, 1.0 / 19.0);
-    T = fma(T, z, 1.0 / 17.0);
-    T = fma(T, z, 1.0 / 15.0);
-    T = fma(T, z, 1.0 / 13.0);
-    T = fma(T, z, 1.0 / 11.0);
-    T = fma(T, z, 1.0 / 9.0);
-    T = fma(T, z, 1.0 / 7.0);
-    T = fma(T, z, 1.0 / 5.0);
-    T = fma(T, z, 1.0 / 3.0);
-    const double c = (2.0 * s_hi) * (z * T);
-    const double L_hi = 2.0 * s_hi;
-    const double L_lo = fma(2.0, s_lo, c);
-    /* step 4: lg = (L_hi + L_lo) / ln 2 */
-    const double g_hi = L_hi * ILN2_HI;
-    double g_lo = fma(L_hi, ILN2_HI, -g_hi);
-    g_lo = fma(L_hi, ILN2_LO, g_lo);
-    g_lo = fma(L_lo, ILN2_HI, g_lo);
-    /* add the exponent: (h, l) = e + g_hi exactly, then l += g_lo */
-    const double ed = (double)e;
-    const double h = ed + g_hi;
-    double l;
-    if (fabs(ed) >= fabs(g_hi)) l = (ed - h) + g_hi;
-    else l = (g_hi - h) + ed;
-    l = l + g_lo;
-    /* t = y (h + l) */
-    const double t_hi = y * h;
-    double t_lo = fma(y, h, -t_hi);
-    t_lo = fma(y, l, t_lo);
-    if (t_hi < -1100.0) return 0.0;
-    if (t_hi > 1100.0) return INFINITY;
-    /* step 5 */
-    const double k = rint(t_hi);
-    const double r0 = t_hi - k; /* exact */
-    const double r_hi = r0 + t_lo;
-    const double r_lo = t_lo - (r_hi - r0);
-    const double u_hi = r_hi * LN2_HI;
-    double u_lo = fma(r_hi, LN2_HI, -u_hi);
-    u_lo = fma(r_hi, LN2_LO, u_lo);
-    u_lo = fma(r_lo, LN2_HI, u_lo);
-    /* E = exp(u) - 1 - u, degree 2..14 in u_hi */
-    double P = 1.0 / 87178291200.0;   /* 1/14! */
-    P = fma(P, u_hi, 1.0 / 6227020800.0); /* 1/13! */
-    P = fma(P, u_hi, 1.0 / 479001600.0);  /* 1/12! */
-    P = fma(P, u_hi, 1.0 / 39916800.0);   /* 1/11! */
-    P = fma(P, u_hi, 1.0 / 3628800.0);    /* 1/10! */
-    P = fma(P, u_hi, 1.0 / 362880.0);     /* 1/9! */
-    P = fma(P, u_hi, 1.0 / 40320.0);      /* 1/8! */
-    P = fma(P, u_hi, 1.0 / 5040.0);       /* 1/7! */
-    P = fma(P, u_hi, 1.0 / 720.0);        /* 1/6! */
-    P = fma(P, u_hi, 1.0 / 120.0);        /* 1/5! */
-    P = fma(P, u_hi, 1.0 / 24.0);         /* 1/4! */
-    P = fma(P, u_hi, 1.0 / 6.0);          /* 1/3! */
-    P = fma(P, u_hi, 0.5);                /* 1/2! */
-    const double E = (u_hi * u_hi) * P;
-    /* m = 1 + u_hi + (u_lo + E) */
-    const double m_hi = 1.0 + u_hi;
-    const double m_err = (1.0 - m_hi) + u_hi; /* exact: |u_hi| < 1 */
-    const double m = m_hi + (m_err + (u_lo + E));
-    const int ki = (int)k;
-    if (ki > 1023) return INFINITY;
-    if (ki < -1074) return 0.0;
-    return m * pow2_d(ki);
+    /* step 6: t 2^64 = Ym Lm 2^(ey + eL + 64) */
+    uint64_t Ym;
+    int ey;
+    decompose_d(y, &Ym, &ey);
+    const u128 p0 = (u128)Ym * (uint64_t)Lm;
+    const u128 p1 = (u128)Ym * (uint64_t)(Lm >> 64);
+    u192 Pt;
+    Pt.lo = p0 + (p1 << 64);
+    Pt.hi = (uint64_t)(p1 >> 64) + (Pt.lo < p0);
+    int bl;
+    if (Pt.hi) bl = 192 - clz64(Pt.hi);
+    else if ((uint64_t)(Pt.lo >> 64)) bl = 128 - clz64((uint64_t)(Pt.lo >> 64));
+    else bl = 64 - clz64((uint64_t)Pt.lo);
+    const int sh = ey + eL + 64;
+    if (bl + sh > 75) return neg ? 0.0 : INFINITY;
+    const u128 T64 = sh >= 0 ? Pt.lo << sh : u192_shr(Pt, -sh);
+    const i128 tq = neg ? -(i128)T64 : (i128)T64;
+    /* step 7 */
+    const i128 kk = (tq + ((i128)1 << 63)) >> 64;
+    const int64_t r = (int64_t)(tq - kk * ((i128)1 << 64));
+    const int64_t u64 = (int64_t)(((i128)r * (i128)LN2_Q63) >> 63);
+    uint64_t fact = 1;
+    int64_t C[16];
+    for (int j = 0; j < 16; ++j) {
+        if (j > 1) fact *= (uint64_t)j;
+        C[j] = (int64_t)((1ull << 62) / fact);
+    }
+    int64_t Pp = C[15];
+    for (int j = 14; j >= 0; --j) Pp = C[j] + (int64_t)(((i128)Pp * u64) >> 64);
+    /* step 8 */
+    const int kt = (int)kk;
+    const int nb = 64 - clz64((uint64_t)Pp);
+    int Er = kt + nb - 63;
+    if (Er > 1023) return INFINITY;
+    int shf;
+    if (Er >= -1022) shf = nb - 53;
+    else shf = 62 - kt - 1074;
+    if (shf >= 64) return 0.0;
+    uint64_t m = (uint64_t)Pp >> shf;
+    const uint64_t rem = (uint64_t)Pp - (m << shf), half = 1ull << (shf - 1);
+    if (rem > half || (rem == half && (m & 1))) m += 1;
+    if (Er >= -1022) {
+        if (m >> 53) { m >>= 1; Er += 1; }
+        if (Er > 1023) return INFINITY;
+        return from_bits_d(((uint64_t)(Er + 1023) << 52) | (m & 0x000fffffffffffffull));
+    }
+    return from_bits_d(m); /* a multiple of 2^-1074 (2^52 is 2^-1022) */
 }
 
 /*
@@ -507,10 +567,10 @@ OR_API double or_lp_d(double h, double ip, double x, double y)
 {
     const double X = fabs(x);
     const double Y = fabs(y);
-    const double m = fmin(X, Y);
-    const double M = fmax(X, Y);
+    const double m = min_d(X, Y);
+    const double M = max_d(X, Y);
     const double q = m / M;
-    const double Q = fmax(q, 0.0);
+    const double Q = max_d(q, 0.0);
     const double S = or_pow_d(Q, h);
     const double Z = fma(S, S, 1.0);
     const double C = or_pow_d(Z, ip);
@@ -521,21 +581,44 @@ OR_API float or_lp_s(float h, float ip, float x, float y)
 {
     const float X = fabsf(x);
     const float Y = fabsf(y);
-    const float m = fminf(X, Y);
-    const float M = fmaxf(X, Y);
+    const float m = min_s(X, Y);
+    const float M = max_s(X, Y);
     const float q = m / M;
-    const float Q = fmaxf(q, 0.0f);
+    const float Q = max_s(q, 0.0f);
     const float S = or_pow_s(Q, h);
     const float Z = fmaf(S, S, 1.0f);
     const float C = or_pow_s(Z, ip);
     return M * C;
 }
 
+/* Elementwise forms of the pow and of v1_lp over arrays (one call per
+ * element of the functions above), so that tests can check many operand
+ * pairs at once. */
+OR_API void or_pow_arr_d(int64_t n, const double *x, const double *y, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_pow_d(x[i], y[i]);
+}
+
+OR_API void or_pow_arr_s(int64_t n, const float *x, const float *y, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_pow_s(x[i], y[i]);
+}
+
+OR_API void or_lp_arr_d(int64_t n, double h, double ip, const double *x, const double *y, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_lp_d(h, ip, x[i], y[i]);
+}
+
+OR_API void or_lp_arr_s(int64_t n, float h, float ip, const float *x, const float *y, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_lp_s(h, ip, x[i], y[i]);
+}
+
 /* p = 1 (Eq. vp1): |x| + |y|.  p = inf (Eq. vpI): max(|x|, |y|), exact. */
 static double sumabs_d(double x, double y) { return fabs(x) + fabs(y); }
 static float sumabs_s(float x, float y) { return fabsf(x) + fabsf(y); }
-static double maxabs_d(double x, double y) { return fmax(fabs(x), fabs(y)); }
-static float maxabs_s(float x, float y) { return fmaxf(fabsf(x), fabsf(y)); }
+static double maxabs_d(double x, double y) { return max_d(fabs(x), fabs(y)); }
+static float maxabs_s(float x, float y) { return max_s(fabsf(x), fabsf(y)); }
 
 typedef struct { int op; double h, ip; } comb_d;
 typedef struct { int op; float h, ip; } comb_s;

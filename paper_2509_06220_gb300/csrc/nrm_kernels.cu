@@ -1008,6 +1008,54 @@ __global__ void k1d_compare_kernel(uint64_t seed, int64_t n, int mode, unsigned 
 
 } // namespace
 
+// Elementwise pow and v1_lp of the tree kernels, for parity tests against
+// the oracle on chosen operands.
+template <typename T> __global__ void pow_eval_kernel(const T *x, const T *y, T *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = pw(x[i], y[i]);
+}
+template <typename T> __global__ void lp_eval_kernel(OpLp<T> op, const T *x, const T *y, T *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = op(x[i], y[i]);
+}
+
+extern "C" nrm_status nrm_test_pow(nrm_dtype dtype, const void *x, const void *y, void *out, int64_t n,
+                                   void *stream) {
+    if (n < 0 || (n > 0 && (!x || !y || !out)) || (dtype != NRM_F64 && dtype != NRM_F32)) return NRM_EINVAL;
+    if (n == 0) return NRM_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (dtype == NRM_F64)
+        pow_eval_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>((const double *)x, (const double *)y,
+                                                                        (double *)out, n);
+    else
+        pow_eval_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>((const float *)x, (const float *)y,
+                                                                       (float *)out, n);
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
+
+extern "C" nrm_status nrm_test_lp(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n,
+                                  void *stream) {
+    if (n < 0 || (n > 0 && (!x || !y || !out)) || !(p > 0.0) || (dtype != NRM_F64 && dtype != NRM_F32))
+        return NRM_EINVAL;
+    if (n == 0) return NRM_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (dtype == NRM_F64) {
+        OpLp<double> op;
+        op.h = p * 0.5;
+        op.ip = 1.0 / p;
+        lp_eval_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>(op, (const double *)x, (const double *)y,
+                                                                       (double *)out, n);
+    } else {
+        OpLp<float> op;
+        const float pf = (float)p;
+        op.h = pf * 0.5f;
+        op.ip = 1.0f / pf;
+        lp_eval_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>(op, (const float *)x, (const float *)y,
+                                                                      (float *)out, n);
+    }
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
+
 extern "C" nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad,
                                            double *example, void *stream) {
     if (n < 0 || !bad || !example) return NRM_EINVAL;

@@ -587,3 +587,110 @@ def test_za_parity(nrm, dt):
     for i, (a, b) in enumerate(pairs):
         want = oracle.cr_hypot(dt(a), dt(b), dt)
         assert bits_equal(o[i], np.asarray(want, dt)), (a, b, o[i], want)
+
+
+# ---------------------------------------------------------------------------
+# the pow and v1_lp combine themselves (Listing 5, Section 4), elementwise
+# ---------------------------------------------------------------------------
+
+def _pow_operands(dt, n, seed):
+    """n (x, y) pairs in families: the two domains v1_lp uses (Q in [0, 1]
+    with y = p/2, Z in [1, 2] with y = 1/p), x near 1 with large y, tiny and
+    subnormal x, results near overflow and underflow, exact powers of two,
+    and raw bit patterns (zero, inf, NaN, subnormal)."""
+    with np.errstate(all="ignore"):
+        return _pow_operand_families(dt, n, seed)
+
+
+def _pow_operand_families(dt, n, seed):
+    rng = np.random.default_rng(seed)
+    k = n // 8
+    it = np.uint64 if dt == np.float64 else np.uint32
+    xs, ys = [], []
+    xs.append(rng.random(k) ** rng.choice([1, 3, 20], k)); ys.append(rng.uniform(0.05, 10, k))
+    xs.append(1 + rng.random(k)); ys.append(1 / rng.uniform(0.05, 40, k))
+    xs.append(1 + rng.uniform(-1, 1, k) * 2.0 ** rng.integers(-52 if dt == np.float64 else -23, 0, k))
+    ys.append(rng.uniform(0.5, 2, k) * 2.0 ** rng.integers(-20, 40, k))
+    lo = -1074 if dt == np.float64 else -149
+    xs.append(rng.uniform(0.5, 2, k) * 2.0 ** rng.integers(lo, lo + 80, k)); ys.append(rng.uniform(0.01, 1.1, k))
+    x4 = rng.uniform(0.1, 4, k)
+    xs.append(x4); ys.append(np.abs(rng.uniform(-1, 1, k) * (1100 if dt == np.float64 else 150)
+                                    / np.maximum(np.abs(np.log2(x4)), 1e-3)) + 1e-3)
+    xs.append(2.0 ** rng.integers(lo, 0, k).astype(np.float64)); ys.append(rng.choice([0.5, 0.25, 1.5, 3.0, 1.0, 7.5], k))
+    nb = 64 if dt == np.float64 else 32
+    raw = rng.integers(0, 2 ** (nb - 1), (2, k), dtype=np.uint64).astype(it)
+    xs.append(raw[0].view(dt).astype(np.float64)); ys.append(raw[1].view(dt).astype(np.float64))
+    rest = n - 7 * k
+    xs.append(rng.random(rest)); ys.append(rng.choice([0.25, 0.75, 1.5, 3.75], rest))
+    return np.concatenate(xs).astype(dt), np.concatenate(ys).astype(dt)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_pow_parity(nrm, dt):
+    """The device pow equals the oracle's bit for bit on 2^20 operand pairs
+    of every family (binary64: the fixed-point integer pow)."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_pow
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    x, y = _pow_operands(dt, 1 << 20, seed=77)
+    xd, yd = dev(x), dev(y)
+    out = torch.empty_like(xd)
+    code = nrm.NRM_F64 if dt == np.float64 else nrm.NRM_F32
+    assert f(code, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()),
+             ctypes.c_void_p(out.data_ptr()), x.size, None) == 0
+    got = out.cpu().numpy()
+    want = oracle.pow_arr(x, y)
+    bad = ~((got.view(np.uint64 if dt == np.float64 else np.uint32) == want.view(np.uint64 if dt == np.float64 else np.uint32))
+            | (np.isnan(got) & np.isnan(want)))
+    assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])
+    assert f(code, None, None, None, -1, None) != 0
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("p", [0.5, 1.5, 3.0, 7.5, math.pi, 2.0 ** 40])
+def test_lp_combine_parity(nrm, dt, p):
+    """v1_lp on the device (binary64: integer quotient and pow, FP64 form for
+    inf, NaN and subnormal operands) equals the oracle's v1_lp bit for bit on
+    2^19 operand pairs: moderate and extreme exponent gaps, equal
+    magnitudes, zeros, subnormals, the largest exponents, and raw bits."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_lp
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_void_p]
+    rng = np.random.default_rng(int(p * 1000) % 2 ** 31)
+    n = 1 << 19
+    k = n // 8
+    emax = 1023 if dt == np.float64 else 127
+    emin = -1074 if dt == np.float64 else -149
+    it = np.uint64 if dt == np.float64 else np.uint32
+    nb = 64 if dt == np.float64 else 32
+    a = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n)
+    b = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n)
+    ea = rng.integers(-30, 30, n)
+    gap = np.concatenate([rng.integers(-3, 4, k), rng.integers(-60, 61, k), rng.integers(-1100, 1100, k),
+                          np.zeros(k, np.int64), rng.integers(-40, 41, n - 4 * k)])
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        x = (a * 2.0 ** ea).astype(dt)
+        y = (b * 2.0 ** np.clip(ea + gap, emin, emax)).astype(dt)
+        y[3 * k:4 * k] = -x[3 * k:4 * k]                      # equal magnitudes
+        x[4 * k:4 * k + 64] = 0                                # zeros
+        y[4 * k + 32:4 * k + 96] = 0
+        x[4 * k + 96:4 * k + 1000] = (a[4 * k + 96:4 * k + 1000] * 2.0 ** (emin + 10)).astype(dt)  # subnormals
+        x[4 * k + 1000:4 * k + 2000] = (a[4 * k + 1000:4 * k + 2000] * 2.0 ** (emax - 1)).astype(dt)
+        raw = rng.integers(0, 2 ** nb, (2, 4000), dtype=np.uint64).astype(it)
+        x[-4000:] = raw[0].view(dt)
+        y[-4000:] = raw[1].view(dt)
+    xd, yd = dev(x), dev(y)
+    out = torch.empty_like(xd)
+    code = nrm.NRM_F64 if dt == np.float64 else nrm.NRM_F32
+    assert f(code, float(p), ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()),
+             ctypes.c_void_p(out.data_ptr()), n, None) == 0
+    got = out.cpu().numpy()
+    want = oracle.lp_arr(p, x, y)
+    ui = np.uint64 if dt == np.float64 else np.uint32
+    bad = ~((got.view(ui) == want.view(ui)) | (np.isnan(got) & np.isnan(want)))
+    assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])

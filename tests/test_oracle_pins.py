@@ -427,27 +427,104 @@ def test_pow_exact_cases():
 
 
 def test_pow_constants_are_correctly_rounded():
-    """The double-word constants ln 2 and 1/ln 2 that the pow uses are
-    (RN(c), RN(c - RN(c))) in each format."""
+    """The binary64 pow's fixed-point constants are 2/ln 2 rounded to Q126,
+    ln 2 rounded to Q63 and ceil(sqrt(2) 2^52); the binary32 pow's double-word
+    constants ln 2 and 1/ln 2 are (RN(c), c - RN(c) to 2^-47)."""
+    import re
     src = open(oracle._build.SRC).read()
 
-    def const(name):
-        import re
+    def macro(name):
         m = re.search(r"#define %s (\S+)" % name, src)
-        return float.fromhex(m.group(1).rstrip("f"))
+        return m.group(1)
 
-    for hi_n, lo_n, c, dt in (("LN2_HI", "LN2_LO", mpmath.log(2), np.float64),
-                              ("ILN2_HI", "ILN2_LO", 1 / mpmath.log(2), np.float64),
-                              ("LN2F_HI", "LN2F_LO", mpmath.log(2), np.float32),
-                              ("ILN2F_HI", "ILN2F_LO", 1 / mpmath.log(2), np.float32)):
+    with mpmath.workprec(400):
+        k126 = int(mpmath.floor(2 / mpmath.log(2) * mpmath.mpf(2) ** 126 + mpmath.mpf("0.5")))
+        ln2q63 = int(mpmath.floor(mpmath.log(2) * mpmath.mpf(2) ** 63 + mpmath.mpf("0.5")))
+        thr = int(mpmath.ceil(mpmath.sqrt(2) * mpmath.mpf(2) ** 52))
+    hexint = lambda t: int(t.rstrip("ull").rstrip("u"), 16)
+    assert (hexint(macro("K126_HI")) << 64) | hexint(macro("K126_LO")) == k126
+    assert hexint(macro("LN2_Q63")) == ln2q63
+    assert hexint(macro("POW_THR")) == thr
+
+    def const(name):
+        return float.fromhex(macro(name).rstrip("f"))
+
+    for hi_n, lo_n, c in (("LN2F_HI", "LN2F_LO", mpmath.log(2)), ("ILN2F_HI", "ILN2F_LO", 1 / mpmath.log(2))):
         hi, lo = const(hi_n), const(lo_n)
-        if dt == np.float64:
-            assert hi == float(mpmath.mpf(c))
-            assert lo == float(c - mpmath.mpf(hi))
-        else:
-            assert hi == float(np.float32(float(c))) or abs(mpmath.mpf(hi) - c) <= mpmath.mpf(2) ** -25
-            assert np.float32(hi) == hi and np.float32(lo) == lo
-            assert abs(mpmath.mpf(hi) + lo - c) < mpmath.mpf(2) ** -47
+        assert hi == float(np.float32(float(c))) or abs(mpmath.mpf(hi) - c) <= mpmath.mpf(2) ** -25
+        assert np.float32(hi) == hi and np.float32(lo) == lo
+        assert abs(mpmath.mpf(hi) + lo - c) < mpmath.mpf(2) ** -47
+
+
+def _bits_d(v):
+    return struct.unpack("<d", struct.pack("<Q", v))[0]
+
+
+def test_pow_d_nearly_correctly_rounded_wide():
+    """The fixed-point binary64 pow stays within 0.6 ulp of x^y (0.5 is the
+    rounding itself) on the wider domain: x near 1 with large y, subnormal x,
+    |y log2 x| up to 1100 (results near the overflow and subnormal limits),
+    and arbitrary bit patterns; results that overflow are +inf and those
+    below 2^-1075 are +0."""
+    r = random.Random(21)
+    worst = 0.0
+    with mpmath.workprec(300):
+        for i in range(4000):
+            kind = i % 6
+            if kind == 0:
+                x = 1 + r.uniform(-1, 1) * 2.0 ** r.randint(-52, -1)
+                y = r.uniform(0.5, 2) * 2.0 ** r.randint(-60, 60)
+            elif kind == 1:
+                x = r.uniform(0.5, 2) * 2.0 ** r.randint(-1074, -1000)
+                y = r.uniform(0.01, 1.1)
+            elif kind == 2:
+                x = r.uniform(0.1, 4)
+                y = abs(r.uniform(-1, 1) * 1100 / max(abs(math.log2(x)), 1e-3)) or 1.0
+            elif kind == 3:
+                x = _bits_d(r.getrandbits(63))
+                y = _bits_d(r.getrandbits(63))
+            elif kind == 4:
+                x = r.random() ** r.choice([1, 3, 20])
+                y = r.uniform(0.01, 12)
+            else:
+                x = 1 + r.random()
+                y = 1 / r.uniform(0.05, 40)
+            if not (math.isfinite(x) and math.isfinite(y)) or x == 0 or y == 0:
+                continue
+            v = float(oracle.pow_(x, y))
+            ex = mpmath.mpf(x) ** mpmath.mpf(y)
+            if ex >= mpmath.mpf(2) ** 1024:
+                assert v == math.inf, (x, y)
+                continue
+            if ex < mpmath.mpf(2) ** -1075:
+                assert v == 0.0, (x, y)
+                continue
+            e = int(mpmath.floor(mpmath.log(ex, 2)))
+            u = mpmath.mpf(2) ** (max(e, -1022) - 52)
+            err = float(abs(mpmath.mpf(v) - ex) / u)
+            worst = max(worst, err)
+            assert err <= 0.6, (x.hex(), y.hex(), err)
+    assert worst > 0.4  # the sample reaches the rounding error itself
+
+
+def test_pow_d_exact_powers_of_two():
+    """pow(2^a, b) = 2^(ab) exactly whenever ab is an integer (step 7 then has
+    r = 0), including the subnormal results, the tie 2^-1075 -> +0 (to even),
+    and the overflow 2^1024 -> +inf; pow(x, 0) = 1; pow(x, inf) = 0 or inf."""
+    for a in range(-1074, 1024, 7):
+        for b in (1.0, 0.5, 2.0, 0.25, 3.0):
+            ab = a * b
+            if ab != int(ab):
+                continue
+            want = math.ldexp(1.0, int(ab)) if -1074 <= ab <= 1023 else (0.0 if ab < -1074 else math.inf)
+            assert float(oracle.pow_(math.ldexp(1.0, a), b)) == want, (a, b)
+    assert float(oracle.pow_(0.5, 1074.0)) == 5e-324
+    assert float(oracle.pow_(0.5, 1075.0)) == 0.0
+    assert float(oracle.pow_(2.0, 1023.0)) == 2.0 ** 1023
+    assert float(oracle.pow_(2.0, 1024.0)) == math.inf
+    for x in (1e-300, 0.3, 1.7, 1e300):
+        assert float(oracle.pow_(x, 0.0)) == 1.0
+        assert float(oracle.pow_(x, math.inf)) == (0.0 if x < 1 else math.inf)
 
 
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
@@ -667,3 +744,24 @@ def test_za_variant(dt):
     one[7] = dt(-2.5)
     assert oracle.nrm_za(one) == oracle.nrm(one) == dt(2.5)
     assert oracle.nrm_za(np.zeros(0, dt)) == 0.0
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_nan_operand_is_missing_data(dt):
+    """Listings 2 and 5 take m = fmin(X, Y) and M = fmax(X, Y); C's Annex F
+    has these treat a NaN argument as missing data, so v1_hypot(NaN, a) =
+    v1_hypot(a, a), v1_lp(NaN, a) = v1_lp(a, a) and max(|NaN|, |a|) = |a|,
+    for quiet and signalling NaNs alike (checked through the array entry
+    points, which keep a signalling NaN's bits)."""
+    ui = np.uint64 if dt == np.float64 else np.uint32
+    qnan, snan = (0x7FF8000000000001, 0x7FF0000000000001) if dt == np.float64 else (0x7FC00001, 0x7F800001)
+    a = np.array([3.0, 1e-30, 0.0, 7.5], dt)
+    for nb in (qnan, snan):
+        nan = np.full(a.shape, nb, ui).view(dt)
+        assert np.isnan(nan).all()
+        for p in (0.5, 3.0, 7.5):
+            assert same_bits(oracle.lp_arr(p, nan, a), oracle.lp_arr(p, a, a))
+            assert same_bits(oracle.lp_arr(p, a, nan), oracle.lp_arr(p, a, a))
+        x = np.concatenate([nan[:1], a[:1]])
+        assert oracle.nrm(x, math.inf) == a[0]
+        assert oracle.nrm(x, 2.0) == oracle.nrm(a[:1].repeat(2), 2.0)
