@@ -178,7 +178,12 @@ def time_batch(nrm, torch, ctx, dev):
     out = {}
     for name, td in (("f64", torch.float64), ("f32", torch.float32)):
         x = nrm.nrm_gen_ragged(offd, seed=0, dtype=td)
-        g = nrm.nrm_batch_graph(x, offd, ctx=ctx)
+        # the batch runs on a context autotuned for this shape (group size,
+        # warps per block, item depth, blocks per SM); the one-launch-per-
+        # vector form keeps the single-vector tuning of `ctx`
+        bctx = nrm.Context(0)
+        tuned = bctx.autotune(nrm.NRM_F64 if td == torch.float64 else nrm.NRM_F32, L)
+        g = nrm.nrm_batch_graph(x, offd, ctx=bctx)
         for _ in range(3):
             g.launch()
         torch.cuda.synchronize()
@@ -207,8 +212,9 @@ def time_batch(nrm, torch, ctx, dev):
                                 "elements": int(off[-1]), "GBps": off[-1] * x.element_size() / (t_graph * 1e-3) / 1e9,
                                 "one_launch_per_vector_ms": t_single,
                                 "one_launch_per_vector_norms_per_s": 4096 / (t_single * 1e-3),
-                                "bitwise_equal_to_single": same}
+                                "bitwise_equal_to_single": same, "tuning": tuned}
         g.close()
+        bctx.close()
         del x
     return out
 

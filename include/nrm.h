@@ -370,6 +370,20 @@ nrm_status nrm_test_pow(nrm_dtype dtype, const void *x, const void *y, void *out
  * NRM_EINVAL for n < 0, null arrays, p <= 0 or NaN, or an unknown dtype. */
 nrm_status nrm_test_lp(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n, void *stream);
 
+/* Test hook: exhaustive checks of the steps of the branch-free binary32
+ * v1_hypot (Listing 2) that the tree kernels use on checked groups, against
+ * the correctly rounded operations.  mode 0: the square root on the
+ * 2^23 + 1 values S in [1, 2] (index i: S = 1 + i 2^-23); mode 1: the FP32
+ * reciprocal estimate's exact scaling with the exponent e in [-88, 124]
+ * (index i: significand i mod 2^23, e = i / 2^23 - 88); mode 2: the division
+ * on the 2^46 significand pairs (index i: a = 1 + (i / 2^23) 2^-23,
+ * b = 1 + (i mod 2^23) 2^-23).  Checks indices [start, start + count);
+ * mismatches are added to *bad (device) and the operands of one of them
+ * stored in example[0..1] (device).  Asynchronous; NRM_EINVAL for a bad mode
+ * or null pointers. */
+nrm_status nrm_test_k1f_exhaustive(int32_t mode, uint64_t start, uint64_t count, unsigned long long *bad,
+                                   float *example, void *stream);
+
 /* Test hook: copy the first `count` ticket counters of the context's
  * workspace to host memory (synchronous).  Between calls they are all zero. */
 nrm_status nrm_test_read_tickets(const nrm_ctx *ctx, uint32_t *host, int64_t count);

@@ -398,8 +398,8 @@ extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
     cudaGetDeviceProperties(&prop, device);
     c->sms = prop.multiProcessorCount;
     // defaults from a sweep on GB300 at n = 2^28 (the autotuner refines them)
-    c->tune[NRM_F32] = nrm_tuning{3, 8, 7, 4};
-    c->tune[NRM_F64] = nrm_tuning{2, 4, 7, 16};
+    c->tune[NRM_F32] = nrm_tuning{3, 4, 9, 8};
+    c->tune[NRM_F64] = nrm_tuning{2, 8, 8, 16};
     nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20, 1 << 16);
     if (s != NRM_OK) {
         delete c;
@@ -1053,6 +1053,67 @@ extern "C" nrm_status nrm_test_lp(nrm_dtype dtype, double p, const void *x, cons
         lp_eval_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>(op, (const float *)x, (const float *)y,
                                                                       (float *)out, n);
     }
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
+
+// Exhaustive checks of k1f_fast's steps against the correctly rounded
+// operations.  mode 0: sqrtf_fast(S) == RN(sqrt(S)) for the 2^23 + 1 values
+// S in [1, 2] (index i: S = 1 + i 2^-23).  mode 1: the FP32 reciprocal
+// estimate scales exactly with the exponent: for significand index i and
+// exponent e in [-88, 124], bits(rcp(M 2^e)) = bits(rcp(M)) - e 2^23.
+// mode 2: divf_fast(a, b) == RN(a/b) for the significand pairs a, b in
+// [1, 2) (index i: a = 1 + (i >> 23) 2^-23, b = 1 + (i & (2^23-1)) 2^-23).
+// Indices [start, start + count) of the mode's range; mismatches are added
+// to *bad and the last one's operands stored in example[0..1].
+__global__ void k1f_exhaustive_kernel(int mode, uint64_t start, uint64_t count, unsigned long long *bad,
+                                      float *example) {
+    unsigned long long nb = 0;
+    float ex0 = 0.0f, ex1 = 0.0f;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = start + t;
+        if (mode == 0) {
+            if (i > (1ull << 23)) continue;
+            const float S = __uint_as_float(0x3f800000u + (uint32_t)i);
+            if (__float_as_uint(sqrtf_fast(S)) != __float_as_uint(__fsqrt_rn(S))) {
+                ++nb;
+                ex0 = S;
+            }
+        } else if (mode == 1) {
+            const uint32_t f = (uint32_t)(i & 0x7fffffu);
+            const int e = (int)(i >> 23) - 88;
+            if (e > 124) continue;
+            const float M0 = __uint_as_float(0x3f800000u | f);
+            const float Me = __uint_as_float((uint32_t)(127 + e) << 23 | f);
+            const int b0 = (int)__float_as_uint(rcp_approx(M0));
+            const int be = (int)__float_as_uint(rcp_approx(Me));
+            if (be != b0 - e * (1 << 23)) {
+                ++nb;
+                ex0 = Me;
+            }
+        } else {
+            if (i >= (1ull << 46)) continue;
+            const float a = __uint_as_float(0x3f800000u | (uint32_t)(i >> 23));
+            const float b = __uint_as_float(0x3f800000u | (uint32_t)(i & 0x7fffffu));
+            if (__float_as_uint(divf_fast(a, b)) != __float_as_uint(__fdiv_rn(a, b))) {
+                ++nb;
+                ex0 = a;
+                ex1 = b;
+            }
+        }
+    }
+    if (nb) {
+        atomicAdd(bad, nb);
+        example[0] = ex0;
+        example[1] = ex1;
+    }
+}
+
+extern "C" nrm_status nrm_test_k1f_exhaustive(int32_t mode, uint64_t start, uint64_t count, unsigned long long *bad,
+                                              float *example, void *stream) {
+    if (mode < 0 || mode > 2 || !bad || !example) return NRM_EINVAL;
+    if (count == 0) return NRM_OK;
+    k1f_exhaustive_kernel<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(mode, start, count, bad, example);
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }
 

@@ -222,9 +222,13 @@ def test_alloc_failure_is_reported(nrm):
     L = nrm.load()
     ctx = nrm.Context(0)
     try:
-        # 2^26 elements need more workspace than a fresh context holds
-        x = nrm.nrm_gen(1 << 26, 8, 0, torch.float64, device=DEV)
-        assert ctx.workspace_bytes(nrm.NRM_F64, x.numel()) > (4 << 20)
+        # the smallest power of two whose workspace exceeds what a fresh
+        # context holds (4 MiB)
+        n = 1 << 24
+        while ctx.workspace_bytes(nrm.NRM_F64, n) <= (4 << 20):
+            n <<= 1
+        assert n <= 1 << 28
+        x = nrm.nrm_gen(n, 8, 0, torch.float64, device=DEV)
         L.nrm_test_inject_alloc_failures(1)
         with pytest.raises(nrm.NrmError) as ei:
             nrm.nrmf(x, ctx=ctx)
@@ -694,3 +698,27 @@ def test_lp_combine_parity(nrm, dt, p):
     ui = np.uint64 if dt == np.float64 else np.uint32
     bad = ~((got.view(ui) == want.view(ui)) | (np.isnan(got) & np.isnan(want)))
     assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_k1f_fast_steps_exhaustive(nrm, mode):
+    """The branch-free binary32 v1_hypot the S trees use on checked groups
+    equals Listing 2's correctly rounded steps: its square root on every S in
+    [1, 2] (mode 0), its division on every pair of significands (mode 2, all
+    2^46 pairs), and the FP32 reciprocal estimate it starts from scales
+    exactly with the exponent over the checked range (mode 1), so the pair
+    test covers every exponent there."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_k1f_exhaustive
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    bad = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ex = torch.zeros(2, dtype=torch.float32, device=DEV)
+    total = {0: (1 << 23) + 1, 1: 213 << 23, 2: 1 << 46}[mode]
+    chunk = 1 << 40
+    for s in range(0, total, chunk):
+        assert f(mode, s, min(chunk, total - s), ctypes.c_void_p(bad.data_ptr()), ctypes.c_void_p(ex.data_ptr()),
+                 None) == 0
+        torch.cuda.synchronize()
+    assert int(bad.item()) == 0, ex.cpu().numpy()
