@@ -722,3 +722,47 @@ def test_k1f_fast_steps_exhaustive(nrm, mode):
                  None) == 0
         torch.cuda.synchronize()
     assert int(bad.item()) == 0, ex.cpu().numpy()
+
+
+@pytest.mark.parametrize("family", ["low_edge", "high_edge", "nan_pairs", "inf", "zeros", "subnormal", "mixed"])
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_checked_group_boundaries(nrm, dt, family):
+    """The S trees combine checked groups with a branch-free v1_hypot and
+    send the others to the general form; results must equal the oracle's
+    whatever values sit in a group: values straddling 2^-88 and 2^118, NaN
+    pairs that meet in the first combine (same lane, adjacent rows), inf,
+    zeros and subnormals, in vectors with full groups, full items and a
+    ragged tail."""
+    n = 5 * (1 << 18) + 77
+    x = inputs.vector(n, seed=40 + len(family), vec=1, dtype=dt)
+    rng = np.random.default_rng(abs(hash((family, str(dt)))) % 2 ** 31)
+    P = 128 if dt == np.float32 else 64
+    pos = rng.choice(n, 64, replace=False)
+    with np.errstate(all="ignore"):
+        if family == "low_edge":
+            x[pos] = (rng.uniform(1, 2, 64) * 2.0 ** rng.integers(-92, -84, 64)).astype(dt)
+        elif family == "high_edge":
+            x[pos] = (rng.uniform(1, 2, 64) * 2.0 ** rng.integers(114, 122, 64)).astype(dt)
+        elif family == "nan_pairs":
+            q = pos[pos + P < n]
+            x[q] = np.nan
+            x[q + P] = np.nan
+        elif family == "inf":
+            x[pos[:4]] = np.inf
+        elif family == "zeros":
+            x[pos] = 0
+            x[:4096] = 0  # whole groups of zeros
+        elif family == "subnormal":
+            tiny = np.finfo(dt).smallest_subnormal
+            x[pos] = (rng.integers(1, 1000, 64) * tiny).astype(dt)
+        else:
+            x[pos[:16]] = (2.0 ** rng.integers(-95, -80, 16)).astype(dt)
+            x[pos[16:32]] = (2.0 ** rng.integers(110, 124, 16)).astype(dt)
+            q = pos[32:40]
+            q = q[q + P < n]
+            x[q] = np.nan
+            x[q + P] = np.nan
+            x[pos[40:48]] = 0
+    got = nrm.nrmf(dev(x)).cpu().numpy()
+    want = oracle.nrm(x)
+    assert bits_equal(np.asarray(got, dt), np.asarray(want, dt)), (family, got, want)
