@@ -370,6 +370,17 @@ nrm_status nrm_test_pow(nrm_dtype dtype, const void *x, const void *y, void *out
  * NRM_EINVAL for n < 0, null arrays, p <= 0 or NaN, or an unknown dtype. */
 nrm_status nrm_test_lp(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n, void *stream);
 
+/* Test hook: the combine the xNRMP tree kernels apply for this p, elementwise:
+ * out[i] = K_p(x[i], y[i]) with K_2 = v1_hypot (Listing 2), K_1 = |x| + |y|
+ * (Eq. vp1), K_p = max(|x|, |y|) for p at or above the cut-off p' (Eq. vpI,
+ * Section 4) and v1_lp (Listing 5) otherwise, in the forms the kernels use
+ * (binary64 v1_hypot and v1_lp without the FP64 divide, square root and
+ * pow).  Device arrays of n elements of
+ * `dtype`; asynchronous on `stream`; NRM_EINVAL for n < 0, null arrays,
+ * p <= 0 or NaN, or an unknown dtype. */
+nrm_status nrm_test_combine(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n,
+                            void *stream);
+
 /* Test hook: exhaustive checks of the steps of the branch-free binary32
  * v1_hypot (Listing 2) that the tree kernels use on checked groups, against
  * the correctly rounded operations.  mode 0: the square root on the

@@ -39,6 +39,8 @@ def lib():
             "or_pow_arr_s": (None, [i64, vp, vp, vp]),
             "or_lp_arr_d": (None, [i64, d, d, vp, vp, vp]),
             "or_lp_arr_s": (None, [i64, f, f, vp, vp, vp]),
+            "or_comb_arr_d": (None, [i64, d, vp, vp, vp]),
+            "or_comb_arr_s": (None, [i64, f, vp, vp, vp]),
             "or_R_d": (d, [i64, vp, d]),
             "or_R_s": (f, [i64, vp, f]),
             "or_R_trace": (i64, [i64, vp]),
@@ -116,6 +118,18 @@ def lp_arr(p, x, y):
         p32 = np.float32(p)
         lib().or_lp_arr_s(xa.size, float(np.float32(p32 * np.float32(0.5))), float(np.float32(np.float32(1) / p32)),
                           xp, yp, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def comb_arr(p, x, y):
+    """Elementwise combine of the tree for p (v1_hypot for p = 2, |x|+|y|
+    for p = 1, max for p at or above the cut-off, else v1_lp)."""
+    dt = np.asarray(x).dtype
+    xa, xp = _arr(x, dt)
+    ya, yp = _arr(y, dt)
+    out = np.empty(xa.shape, dt)
+    f = lib().or_comb_arr_d if dt == np.float64 else lib().or_comb_arr_s
+    f(xa.size, float(p) if dt == np.float64 else float(np.float32(p)), xp, yp, out.ctypes.data_as(ctypes.c_void_p))
     return out
 
 

@@ -674,6 +674,20 @@ static comb_s comb_for_s(float p)
     return c;
 }
 
+/* The combine the tree applies for p (Eq. vp1, v1_hypot, v1_lp, Eq. vpI with
+ * the cut-off of Section 4), elementwise over arrays, for tests. */
+OR_API void or_comb_arr_d(int64_t n, double p, const double *x, const double *y, double *out)
+{
+    const comb_d c = comb_for_d(p);
+    for (int64_t i = 0; i < n; ++i) out[i] = comb_apply_d(&c, x[i], y[i]);
+}
+
+OR_API void or_comb_arr_s(int64_t n, float p, const float *x, const float *y, float *out)
+{
+    const comb_s c = comb_for_s(p);
+    for (int64_t i = 0; i < n; ++i) out[i] = comb_apply_s(&c, x[i], y[i]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* R_x: the scalar recursion of Listing 1 / Eq. r                           */
 /* ------------------------------------------------------------------------ */

@@ -1033,6 +1033,33 @@ extern "C" nrm_status nrm_test_pow(nrm_dtype dtype, const void *x, const void *y
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }
 
+template <typename T, class Op> __global__ void combine_eval_kernel(Op op, const T *x, const T *y, T *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = op(x[i], y[i]);
+}
+
+extern "C" nrm_status nrm_test_combine(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n,
+                                       void *stream) {
+    if (n < 0 || (n > 0 && (!x || !y || !out)) || !(p > 0.0) || (dtype != NRM_F64 && dtype != NRM_F32))
+        return NRM_EINVAL;
+    if (n == 0) return NRM_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    cudaError_t e;
+    if (dtype == NRM_F64)
+        e = with_op<double>(p, [&](auto op) {
+            combine_eval_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>(op, (const double *)x,
+                                                                             (const double *)y, (double *)out, n);
+            return cudaGetLastError();
+        });
+    else
+        e = with_op<float>((float)p, [&](auto op) {
+            combine_eval_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>(op, (const float *)x,
+                                                                            (const float *)y, (float *)out, n);
+            return cudaGetLastError();
+        });
+    return e == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
+
 extern "C" nrm_status nrm_test_lp(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n,
                                   void *stream) {
     if (n < 0 || (n > 0 && (!x || !y || !out)) || !(p > 0.0) || (dtype != NRM_F64 && dtype != NRM_F32))

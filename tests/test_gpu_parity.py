@@ -766,3 +766,63 @@ def test_checked_group_boundaries(nrm, dt, family):
     got = nrm.nrmf(dev(x)).cpu().numpy()
     want = oracle.nrm(x)
     assert bits_equal(np.asarray(got, dt), np.asarray(want, dt)), (family, got, want)
+
+
+def _combine_operands(dt, n, seed):
+    """Operand pairs for the combine functors: moderate and huge exponent
+    gaps, equal and adjacent magnitudes, sums that carry into the next
+    binade or round to even, subnormals (both, one), the largest finite
+    values (sums overflowing to inf), zeros, and raw bit patterns."""
+    rng = np.random.default_rng(seed)
+    it, nb = (np.uint64, 64) if dt == np.float64 else (np.uint32, 32)
+    emax = 1023 if dt == np.float64 else 127
+    sub = np.finfo(dt).smallest_subnormal
+    k = n // 8
+    with np.errstate(all="ignore"):
+        a = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n)
+        b = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n)
+        ea = rng.integers(-60, 60, n)
+        gap = np.concatenate([rng.integers(-3, 4, k), rng.integers(-70, 71, k), rng.integers(50, 60, k),
+                              np.zeros(k, np.int64), rng.integers(-30, 31, n - 4 * k)])
+        x = (a * 2.0 ** ea).astype(dt)
+        y = (b * 2.0 ** (ea - gap)).astype(dt)
+        y[3 * k:3 * k + k // 2] = -x[3 * k:3 * k + k // 2]                         # equal magnitudes
+        y[3 * k + k // 2:4 * k] = np.nextafter(x[3 * k + k // 2:4 * k], dt(np.inf))  # adjacent
+        s0 = 4 * k
+        x[s0:s0 + 2000] = (rng.integers(1, 2 ** 20, 2000) * sub).astype(dt)          # subnormal pairs
+        y[s0:s0 + 2000] = (rng.integers(1, 2 ** 20, 2000) * sub).astype(dt)
+        x[s0 + 2000:s0 + 4000] = (rng.integers(1, 2 ** 20, 2000) * sub).astype(dt)   # subnormal + normal
+        big = np.finfo(dt).max
+        x[s0 + 4000:s0 + 6000] = (big * rng.uniform(0.5, 1, 2000)).astype(dt)         # overflow to inf
+        y[s0 + 4000:s0 + 6000] = (big * rng.uniform(0.5, 1, 2000)).astype(dt)
+        x[s0 + 6000:s0 + 6100] = 0
+        y[s0 + 6050:s0 + 6150] = 0
+        raw = rng.integers(0, 2 ** nb, (2, 8000), dtype=np.uint64).astype(it)
+        x[-8000:] = raw[0].view(dt)
+        y[-8000:] = raw[1].view(dt)
+    return x, y
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("p", [1.0, 2.0, math.inf, 2.0 ** 60, 3.0])
+def test_combine_parity(nrm, dt, p):
+    """Every combine the trees apply (|x|+|y|, v1_hypot, max(|x|,|y|), v1_lp;
+    for binary64 the forms without the FP64 pipe) equals the oracle's combine
+    for the same p bit for bit on 2^19 operand pairs."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_combine
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_void_p]
+    x, y = _combine_operands(dt, 1 << 19, seed=int(min(p, 1e6) * 7) + 5)
+    xd, yd = dev(x), dev(y)
+    out = torch.empty_like(xd)
+    code = nrm.NRM_F64 if dt == np.float64 else nrm.NRM_F32
+    assert f(code, float(p), ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()),
+             ctypes.c_void_p(out.data_ptr()), x.size, None) == 0
+    got = out.cpu().numpy()
+    want = oracle.comb_arr(p, x, y)
+    ui = np.uint64 if dt == np.float64 else np.uint32
+    bad = ~((got.view(ui) == want.view(ui)) | (np.isnan(got) & np.isnan(want)))
+    assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])
