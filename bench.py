@@ -45,7 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the ncu traffic figures in profiles/ belong to the kernel build they were
 # captured on; set to False whenever the binary64 tree kernel changes
 TRAFFIC_VALID = True
-TRAFFIC_2E26 = 537.110016e6 + 7.140352e6  # DRAM read + write of one launch at n = 2^26
+TRAFFIC_D_2E28 = 2147.770e6 + 10.934272e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1073.890e6 + 7.412224e6  # SNRMF: the same
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -336,9 +337,9 @@ def main():
     d_bytes_gbs = BYTES_D / (d_avg * 1e-3) / 1e9
     s_bytes_gbs = BYTES_S / (s_avg * 1e-3) / 1e9
     achieved_ops = 7 * hypot_d / (d_avg * 1e-3)
-    # DRAM bytes read+written per launch: ncu capture at n = 2^26 scaled by 4
-    # (traffic is proportional to n); see profiles/tree_kernel_small_2e26_full.md
-    traffic = TRAFFIC_2E26 * (N / float(1 << 26)) if TRAFFIC_VALID else None
+    # DRAM bytes read+written per launch from an ncu capture at n = 2^28
+    # (profiles/tree_kernel_nrmf_2e28_full.md), in proportion to n otherwise
+    traffic = TRAFFIC_D_2E28 * (N / float(1 << 28)) if TRAFFIC_VALID else None
     roof = {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": fp64_ops_peak / 1e9,
             "unit": "Gop/s (FP64, 7 per v1_hypot)", "frac": achieved_ops / fp64_ops_peak, "traffic": traffic,
             "kernel": "tree_kernel<double,%d,OpHypot>" % ctx.tuning_for(nrm.NRM_F64).group_log2,
@@ -359,7 +360,8 @@ def main():
                                 "Ghypot_per_s": hypot_d / (d_avg * 1e-3) / 1e9,
                                 "fp64_pipe_peak_Gops": fp64_ops_peak / 1e9},
                       "snrmf": {"ms": s_avg, "GBps": s_bytes_gbs, "Gelem_per_s": N / (s_avg * 1e-3) / 1e9,
-                                "hbm_frac": s_bytes_gbs / hbm_peak}}}
+                                "hbm_frac": s_bytes_gbs / hbm_peak,
+                                "traffic": TRAFFIC_S_2E28 * (N / float(1 << 28)) if TRAFFIC_VALID else None}}}
 
     # end to end through the host-buffer entry point
     if not args.no_e2e:
