@@ -727,22 +727,23 @@ def test_k1f_fast_steps_exhaustive(nrm, mode):
 @pytest.mark.parametrize("family", ["low_edge", "high_edge", "nan_pairs", "inf", "zeros", "subnormal", "mixed"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 def test_checked_group_boundaries(nrm, dt, family):
-    """The S trees combine checked groups with a branch-free v1_hypot and
-    send the others to the general form; results must equal the oracle's
-    whatever values sit in a group: values straddling 2^-88 and 2^118, NaN
-    pairs that meet in the first combine (same lane, adjacent rows), inf,
-    zeros and subnormals, in vectors with full groups, full items and a
-    ragged tail."""
+    """The trees combine checked groups with a branch-free v1_hypot and send
+    the others to the general form; results must equal the oracle's whatever
+    values sit in a group: values straddling the ends of the checked range
+    (binary32 2^-88 and 2^118, binary64 2^-500 and 2^494), NaN pairs that
+    meet in the first combine (same lane, adjacent rows), inf, zeros and
+    subnormals, in vectors with full groups, full items and a ragged tail."""
     n = 5 * (1 << 18) + 77
     x = inputs.vector(n, seed=40 + len(family), vec=1, dtype=dt)
     rng = np.random.default_rng(abs(hash((family, str(dt)))) % 2 ** 31)
     P = 128 if dt == np.float32 else 64
     pos = rng.choice(n, 64, replace=False)
+    lo, hi = (-88, 118) if dt == np.float32 else (-500, 494)
     with np.errstate(all="ignore"):
         if family == "low_edge":
-            x[pos] = (rng.uniform(1, 2, 64) * 2.0 ** rng.integers(-92, -84, 64)).astype(dt)
+            x[pos] = (rng.uniform(1, 2, 64) * 2.0 ** rng.integers(lo - 4, lo + 4, 64)).astype(dt)
         elif family == "high_edge":
-            x[pos] = (rng.uniform(1, 2, 64) * 2.0 ** rng.integers(114, 122, 64)).astype(dt)
+            x[pos] = (rng.uniform(1, 2, 64) * 2.0 ** rng.integers(hi - 4, hi + 4, 64)).astype(dt)
         elif family == "nan_pairs":
             q = pos[pos + P < n]
             x[q] = np.nan
@@ -756,8 +757,8 @@ def test_checked_group_boundaries(nrm, dt, family):
             tiny = np.finfo(dt).smallest_subnormal
             x[pos] = (rng.integers(1, 1000, 64) * tiny).astype(dt)
         else:
-            x[pos[:16]] = (2.0 ** rng.integers(-95, -80, 16)).astype(dt)
-            x[pos[16:32]] = (2.0 ** rng.integers(110, 124, 16)).astype(dt)
+            x[pos[:16]] = (2.0 ** rng.integers(lo - 7, lo + 8, 16)).astype(dt)
+            x[pos[16:32]] = (2.0 ** rng.integers(hi - 8, hi + 6, 16)).astype(dt)
             q = pos[32:40]
             q = q[q + P < n]
             x[q] = np.nan
