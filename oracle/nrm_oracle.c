@@ -57,12 +57,16 @@ typedef long double q128; /* IEEE binary128 on AArch64 Linux */
 #define Q_SQRT sqrtl
 #define Q_POW powl
 #define Q_FABS fabsl
+#define Q_LOG2 log2l
+#define Q_FLOOR floorl
 #elif defined(__x86_64__)
 #include <quadmath.h>
 typedef __float128 q128;
 #define Q_SQRT sqrtq
 #define Q_POW powq
 #define Q_FABS fabsq
+#define Q_LOG2 log2q
+#define Q_FLOOR floorq
 #else
 #error "binary128 reference needs AArch64 long double or x86-64 __float128"
 #endif
@@ -315,42 +319,46 @@ static float pow2_s(int k)
 /*
  * or_pow_d(x, y) ~ x^y for x >= 0 and y > 0: the binary64 pow of Listing 5.
  * The paper leaves the pow to the platform (cr_pow, __builtin_pow, SLEEF);
- * this one is defined here in fixed-point integer arithmetic from start to
- * end, so that the oracle and the GPU compute the same bits and the pow
- * needs no FP64 operation.  A "Qk" integer v stands for v 2^-k; every right
- * shift is a floor.  Steps:
- *  1. x = M 2^(E-52) with M in [2^52, 2^53); if M >= THR = ceil(sqrt2 2^52)
- *     then f = M/2^53 and E += 1, else f = M/2^52 (f in [1/sqrt2, sqrt2)).
- *  2. s = (f-1)/(f+1) = num/den with num = M - 2^k and den = M + 2^k exact
- *     (2^k the divisor of step 1).  |s| = Qs 2^es with Qs the 128-bit floor
- *     quotient floor(An 2^128 / Dn) of An = |num| 2^la and Dn = den 2^ld,
- *     both normalised to [2^63, 2^64) (An halved first when not below Dn).
- *  3. atanh(s) = s W, W = 1 + z T(z), z = s^2, T(z) = sum_{j=0}^{10}
- *     z^j/(2j+3): z in Q69 from the top word of Qs, T by Horner in Q65 with
- *     coefficients floor(2^65/(2j+3)), w = z T in Q70 (|s| <= 0.1716, the
- *     first omitted term z^12/25 is below 2^-65).
- *  4. log2 f = 2 atanh(s)/ln 2 = s W K with K = 2/ln 2 rounded to Q126:
- *     V = Qs/2 + floor(Qs/2 w) (129 bits never needed), Gm = the top 128
- *     bits of V K (the three high partial products).
- *  5. log2 x = E + log2 f: for E != 0 a Q116 fixed-point sum (|E| <= 1075,
- *     |log2 f| <= 1/2); for E = 0 the 128-bit Gm with its exponent.
- *  6. t = y log2 x: y's 53-bit significand times the 128-bit log2 x exactly
- *     (192 bits), then truncated to Q64; |t| >= 2^11 overflows (log2 x > 0)
- *     or underflows (log2 x < 0).
- *  7. t = k + r with k = floor(t + 1/2) and r in [-1/2, 1/2) in Q64;
- *     u = r ln 2 in Q64 (ln 2 rounded to Q63); e^u by its Taylor series to
- *     degree 15, Horner in Q62 with coefficients floor(2^62/j!)
- *     (|u| <= 0.347, the first omitted term is below 2^-68).
- *  8. x^y = e^u 2^k rounded to nearest (ties to even) to 53 bits, or to a
+ * this one is defined here in fixed-point integer arithmetic, with a
+ * table-driven reduction in the manner of Tang's table-driven log and exp,
+ * so that the oracle and the GPU compute the same bits and the pow needs no
+ * FP64 operation.  A "Qk" integer v stands for v 2^-k; every right shift
+ * of a magnitude is a floor.  Steps:
+ *  1. x = M 2^(E-52), M in [2^52, 2^53).  j = the top 8 fraction bits of M;
+ *     the reference significand is C_j = 2^52 + j 2^44 for j < 128 and
+ *     2^52 + (j + 1) 2^44 for j >= 128 (then E += 1: f = M/2^53), so that
+ *     x = 2^E F_j (1 + u) with F_j = C_j/2^52 or C_j/2^53 and
+ *     u = (M - C_j)/C_j, |u| < 2^-8, u >= 0 below j = 128, u <= 0 above,
+ *     and F_0 = F_255 = 1 (no cancellation next to x = 1).
+ *  2. a = |u| = g/C_j with g = |M - C_j|: the normalised g (gn = g 2^lg)
+ *     times R_j = RN(2^179/C_j) (128 bits), top 128 bits: a = Up 2^-(115+lg).
+ *  3. log(1 + u) = a - a^2 Hp(a) (u >= 0) or -(a + a^2 Hm(a)) (u < 0) with
+ *     Hp, Hm = sum_{i=0}^{7} (-+a)^i/(i+2) by Horner in Q63 (coefficients
+ *     floor(2^63/(i+2)), a in Q71): the series of log(1+u) to u^9/9 (the
+ *     first omitted term is below 2^-72 of it).  a^2 H from the top words
+ *     (Uh^2 then times H), aligned to a's scale and added: L1m 2^-(115+lg).
+ *  4. log2(1 + u) = L1m ILN2 (ILN2 = RN(2^127/ln 2), 128 bits; the three
+ *     high partial products) = L2m 2^-(114+lg).
+ *  5. log2 x = E + T_j + log2(1+u), T_j = RN(log2(F_j) 2^80): a Q116
+ *     fixed-point sum, or, when E = 0 and T_j = 0 (x within 2^-8 of 1),
+ *     the 128-bit L2m with its exponent (full relative precision).
+ *  6. t = y log2 x from y's 53-bit significand (192-bit product), truncated
+ *     to Q64; |t| >= 2^11 overflows or underflows.
+ *  7. k = floor(t), r = t - k = i/64 + rho (i = top 6 bits of r, rho <
+ *     2^-6); v = rho ln 2 in Q70 (ln 2 = RN(2^64 ln 2)); e^v by its Taylor
+ *     series to degree 7, Horner in Q63 (floor(2^63/k!)); 2^r = TE_i e^v
+ *     with TE_i = RN(2^(i/64) 2^63) (a Q126 product).
+ *  8. 2^k 2^r rounded to nearest (ties to even) to 53 bits, or to a
  *     multiple of 2^-1074 below 2^-1022; above 2^1024 it is +inf.
+ * The tables: R_j by exact long division; T_j and TE_i from binary128 log2
+ * and pow, rounded to nearest (pinned to the 400-bit values in the tests).
  * Exact cases: pow(0,y) = 0, pow(1,y) = 1, pow(inf,y) = inf, pow(x,0) = 1,
  * pow(x,inf) = 0 (x < 1) or inf (x > 1), and pow(2^a, b) = 2^(ab) whenever
- * ab is an integer (then r = 0 and e^u = 1 exactly).
+ * ab is an integer (then u = 0, T_j = 0, r = 0 and TE_0 e^0 = 2^126).
  */
-#define POW_THR 0x16a09e667f3bcdull /* ceil(sqrt(2) 2^52) */
-#define K126_HI 0xb8aa3b295c17f0bbull /* RN(2/ln2 2^126), high word */
-#define K126_LO 0xbe87fed0691d3e89ull /* low word */
-#define LN2_Q63 0x58b90bfbe8e7bcd6ull /* RN(ln2 2^63) */
+#define PW_ILN2_HI 0xb8aa3b295c17f0bbull /* RN(2^127 / ln 2), high word */
+#define PW_ILN2_LO 0xbe87fed0691d3e89ull /* low word */
+#define PW_LN2 0xb17217f7d1cf79acull     /* RN(2^64 ln 2) */
 
 typedef __int128 i128;
 
@@ -365,6 +373,60 @@ static u128 u192_shr(u192 v, int s)
     return (v.lo >> s) | ((u128)v.hi << (128 - s));
 }
 
+static uint64_t pw_C(int j) { return (1ull << 52) + ((uint64_t)(j + (j >= 128 ? 1 : 0)) << 44); }
+
+static u128 PW_R[256];
+static i128 PW_T[256];
+static uint64_t PW_TE[64];
+static pthread_once_t pw_once = PTHREAD_ONCE_INIT;
+
+static void pw_init(void)
+{
+    for (int j = 0; j < 256; ++j) {
+        const uint64_t C = pw_C(j);
+        /* R_j = RN(2^179 / C): restoring long division of 2^179 by C */
+        u128 q = 0;
+        uint64_t r = 0;
+        for (int b = 179; b >= 0; --b) {
+            r = 2 * r + (b == 179 ? 1 : 0);
+            q <<= 1;
+            if (r >= C) { r -= C; q |= 1; }
+        }
+        if (2 * r >= C) q += 1; /* no ties: C is not a power of two unless r = 0 */
+        PW_R[j] = q;
+        /* T_j = RN(log2(F_j) 2^80) */
+        const q128 F = (q128)C / (j >= 128 ? (q128)9007199254740992.0 : (q128)4503599627370496.0);
+        const q128 L = Q_LOG2(F) * (q128)1208925819614629174706176.0; /* 2^80 */
+        PW_T[j] = (i128)Q_FLOOR(L + (q128)0.5);
+    }
+    for (int i = 0; i < 64; ++i) {
+        const q128 v = Q_POW((q128)2, (q128)i / 64) * (q128)9223372036854775808.0; /* 2^63 */
+        PW_TE[i] = (uint64_t)Q_FLOOR(v + (q128)0.5);
+    }
+}
+
+/* the tables, for the tests (R as {hi, lo}, T as two's complement {hi, lo}) */
+OR_API void or_pow_tables_d(uint64_t *R, uint64_t *T, uint64_t *TE)
+{
+    pthread_once(&pw_once, pw_init);
+    for (int j = 0; j < 256; ++j) {
+        R[2 * j] = (uint64_t)(PW_R[j] >> 64);
+        R[2 * j + 1] = (uint64_t)PW_R[j];
+        T[2 * j] = (uint64_t)((u128)PW_T[j] >> 64);
+        T[2 * j + 1] = (uint64_t)(u128)PW_T[j];
+    }
+    for (int i = 0; i < 64; ++i) TE[i] = PW_TE[i];
+}
+
+/* RN(P / 2^s), ties to even, for 1 <= s < 128 */
+static u128 rne_shr(u128 P, int s)
+{
+    u128 q = P >> s;
+    const u128 rem = P - (q << s), half = (u128)1 << (s - 1);
+    if (rem > half || (rem == half && (q & 1))) q += 1;
+    return q;
+}
+
 OR_API double or_pow_d(double x, double y)
 {
     if (isnan(x) || isnan(y)) return x + y;
@@ -373,64 +435,54 @@ OR_API double or_pow_d(double x, double y)
     if (isinf(x)) return x;
     if (y == 0.0) return 1.0;
     if (isinf(y)) return x < 1.0 ? 0.0 : INFINITY;
+    pthread_once(&pw_once, pw_init);
     /* step 1 */
     uint64_t M;
     int E;
     decompose_d(x, &M, &E);
     E += 52;
-    int k = 52;
-    if (M >= POW_THR) { k = 53; E += 1; }
-    /* steps 2-5: log2 x = (neg ? -1 : 1) Lm 2^eL */
-    const int64_t num = (int64_t)M - (int64_t)(1ull << k);
-    const uint64_t den = M + (1ull << k);
+    const int j = (int)((M >> 44) & 255);
+    const int up = j >= 128;
+    E += up;
+    const uint64_t C = pw_C(j);
+    const uint64_t g = up ? C - M : M - C;
+    /* steps 2-4: log2(1 + u) = (up ? -1 : 1) L2m 2^L2e */
+    u128 L2m = 0;
+    int lg = 0;
+    if (g != 0) {
+        lg = clz64(g);
+        const uint64_t gn = g << lg;
+        const u128 R = PW_R[j];
+        const u128 Up = (u128)gn * (uint64_t)(R >> 64) + (((u128)gn * (uint64_t)R) >> 64);
+        const uint64_t a71 = (uint64_t)(Up >> (44 + lg));
+        uint64_t H = (1ull << 63) / 9;
+        for (int i = 6; i >= 0; --i) {
+            const uint64_t t = (uint64_t)(((u128)H * a71) >> 64) >> 7;
+            const uint64_t c = (1ull << 63) / (uint64_t)(i + 2);
+            H = up ? c + t : c - t;
+        }
+        const uint64_t Uh = (uint64_t)(Up >> 64);
+        const uint64_t S2 = (uint64_t)(((u128)Uh * Uh) >> 64);
+        const uint64_t Wq = (uint64_t)(((u128)S2 * H) >> 64);
+        const u128 Wa = (u128)Wq << (78 - lg);
+        const u128 L1m = up ? Up + Wa : Up - Wa;
+        const uint64_t Lh = (uint64_t)(L1m >> 64), Ll = (uint64_t)L1m;
+        L2m = (u128)Lh * PW_ILN2_HI + (((u128)Lh * PW_ILN2_LO) >> 64) + (((u128)Ll * PW_ILN2_HI) >> 64);
+    }
+    /* step 5: log2 x = (neg ? -1 : 1) Lm 2^eL */
     u128 Lm;
     int eL;
     int neg;
-    if (num == 0) {
-        neg = E < 0;
-        Lm = (u128)(uint64_t)(E < 0 ? -E : E) << 116;
-        eL = -116;
+    if (E == 0 && PW_T[j] == 0) {
+        Lm = L2m;
+        eL = -(114 + lg);
+        neg = up;
     } else {
-        neg = num < 0;
-        const uint64_t A = (uint64_t)(num < 0 ? -num : num);
-        const int la = clz64(A), ld = clz64(den);
-        uint64_t An = A << la;
-        const uint64_t Dn = den << ld;
-        int es = -128 + ld - la;
-        if (An >= Dn) { An >>= 1; es += 1; }
-        /* step 2: Qs = floor(An 2^128 / Dn) in two 64-bit digits */
-        const u128 N1 = (u128)An << 64;
-        const uint64_t q1 = (uint64_t)(N1 / Dn);
-        const uint64_t r1 = (uint64_t)(N1 % Dn);
-        const uint64_t q0 = (uint64_t)(((u128)r1 << 64) / Dn);
-        const u128 Qs = ((u128)q1 << 64) | q0;
-        const int sig = -(es + 128); /* |s| in [2^-(sig+1), 2^-sig) */
-        /* step 3 */
-        const u128 P = (u128)q1 * q1;
-        const int zs = 59 + 2 * sig;
-        const uint64_t z69 = zs < 128 ? (uint64_t)(P >> zs) : 0;
-        u128 T = ((u128)1 << 65) / 23;
-        for (int j = 9; j >= 0; --j)
-            T = ((u128)1 << 65) / (uint64_t)(2 * j + 3) + ((T * z69) >> 69);
-        const uint64_t w70 = (uint64_t)((T * z69) >> 64);
-        /* step 4 */
-        const u128 Qh = Qs >> 1;
-        const u128 V = Qh + ((((u128)(uint64_t)(Qh >> 64) * w70) + (((u128)(uint64_t)Qh * w70) >> 64)) >> 6);
-        const uint64_t Vh = (uint64_t)(V >> 64), Vl = (uint64_t)V;
-        const u128 Gm = (u128)Vh * K126_HI + (((u128)Vh * K126_LO) >> 64) + (((u128)Vl * K126_HI) >> 64);
-        const int eG = es + 3;
-        /* step 5 */
-        if (E == 0) {
-            Lm = Gm;
-            eL = eG;
-        } else {
-            const int sh = -(eG + 116);
-            const u128 g = sh < 128 ? Gm >> sh : 0;
-            const u128 base = (u128)(uint64_t)(E < 0 ? -E : E) << 116;
-            Lm = ((E < 0) == neg) ? base + g : base - g;
-            eL = -116;
-            neg = E < 0;
-        }
+        const u128 l2 = g != 0 ? L2m >> (lg - 2) : 0;
+        const i128 Lq = (i128)E * ((i128)1 << 116) + PW_T[j] * ((i128)1 << 36) + (up ? -(i128)l2 : (i128)l2);
+        neg = Lq < 0;
+        Lm = neg ? (u128)(-Lq) : (u128)Lq;
+        eL = -116;
     }
     /* step 6: t 2^64 = Ym Lm 2^(ey + eL + 64) */
     uint64_t Ym;
@@ -450,35 +502,31 @@ OR_API double or_pow_d(double x, double y)
     const u128 T64 = sh >= 0 ? Pt.lo << sh : u192_shr(Pt, -sh);
     const i128 tq = neg ? -(i128)T64 : (i128)T64;
     /* step 7 */
-    const i128 kk = (tq + ((i128)1 << 63)) >> 64;
-    const int64_t r = (int64_t)(tq - kk * ((i128)1 << 64));
-    const int64_t u64 = (int64_t)(((i128)r * (i128)LN2_Q63) >> 63);
-    uint64_t fact = 1;
-    int64_t C[16];
-    for (int j = 0; j < 16; ++j) {
-        if (j > 1) fact *= (uint64_t)j;
-        C[j] = (int64_t)((1ull << 62) / fact);
+    const int k = (int)(tq >> 64);
+    const uint64_t r = (uint64_t)tq;
+    const int i = (int)(r >> 58);
+    const uint64_t rho = r & ((1ull << 58) - 1);
+    const uint64_t v70 = (uint64_t)(((u128)rho * PW_LN2) >> 58);
+    uint64_t fact = 5040; /* 7! */
+    uint64_t Ev = (1ull << 63) / fact;
+    for (int kk = 6; kk >= 0; --kk) {
+        fact = kk > 1 ? fact / (uint64_t)(kk + 1) : 1;
+        Ev = (1ull << 63) / fact + ((uint64_t)(((u128)Ev * v70) >> 64) >> 6);
     }
-    int64_t Pp = C[15];
-    for (int j = 14; j >= 0; --j) Pp = C[j] + (int64_t)(((i128)Pp * u64) >> 64);
+    const u128 P = (u128)PW_TE[i] * Ev; /* Q126 */
     /* step 8 */
-    const int kt = (int)kk;
-    const int nb = 64 - clz64((uint64_t)Pp);
-    int Er = kt + nb - 63;
+    const int nb = (uint64_t)(P >> 64) ? 128 - clz64((uint64_t)(P >> 64)) : 64 - clz64((uint64_t)P);
+    int Er = k + nb - 127;
     if (Er > 1023) return INFINITY;
-    int shf;
-    if (Er >= -1022) shf = nb - 53;
-    else shf = 62 - kt - 1074;
-    if (shf >= 64) return 0.0;
-    uint64_t m = (uint64_t)Pp >> shf;
-    const uint64_t rem = (uint64_t)Pp - (m << shf), half = 1ull << (shf - 1);
-    if (rem > half || (rem == half && (m & 1))) m += 1;
     if (Er >= -1022) {
+        uint64_t m = (uint64_t)rne_shr(P, nb - 53);
         if (m >> 53) { m >>= 1; Er += 1; }
         if (Er > 1023) return INFINITY;
         return from_bits_d(((uint64_t)(Er + 1023) << 52) | (m & 0x000fffffffffffffull));
     }
-    return from_bits_d(m); /* a multiple of 2^-1074 (2^52 is 2^-1022) */
+    const int shf = 126 - k - 1074;
+    if (shf >= 128) return 0.0;
+    return from_bits_d((uint64_t)rne_shr(P, shf)); /* a multiple of 2^-1074 (2^52 is 2^-1022) */
 }
 
 /*

@@ -427,9 +427,9 @@ def test_pow_exact_cases():
 
 
 def test_pow_constants_are_correctly_rounded():
-    """The binary64 pow's fixed-point constants are 2/ln 2 rounded to Q126,
-    ln 2 rounded to Q63 and ceil(sqrt(2) 2^52); the binary32 pow's double-word
-    constants ln 2 and 1/ln 2 are (RN(c), c - RN(c) to 2^-47)."""
+    """The binary64 pow's fixed-point constants are 2^127/ln 2 and 2^64 ln 2
+    rounded to nearest; the binary32 pow's double-word constants ln 2 and
+    1/ln 2 are (RN(c), c - RN(c) to 2^-47)."""
     import re
     src = open(oracle._build.SRC).read()
 
@@ -438,13 +438,11 @@ def test_pow_constants_are_correctly_rounded():
         return m.group(1)
 
     with mpmath.workprec(400):
-        k126 = int(mpmath.floor(2 / mpmath.log(2) * mpmath.mpf(2) ** 126 + mpmath.mpf("0.5")))
-        ln2q63 = int(mpmath.floor(mpmath.log(2) * mpmath.mpf(2) ** 63 + mpmath.mpf("0.5")))
-        thr = int(mpmath.ceil(mpmath.sqrt(2) * mpmath.mpf(2) ** 52))
+        iln2 = int(mpmath.floor(mpmath.mpf(2) ** 127 / mpmath.log(2) + mpmath.mpf("0.5")))
+        ln2 = int(mpmath.floor(mpmath.log(2) * mpmath.mpf(2) ** 64 + mpmath.mpf("0.5")))
     hexint = lambda t: int(t.rstrip("ull").rstrip("u"), 16)
-    assert (hexint(macro("K126_HI")) << 64) | hexint(macro("K126_LO")) == k126
-    assert hexint(macro("LN2_Q63")) == ln2q63
-    assert hexint(macro("POW_THR")) == thr
+    assert (hexint(macro("PW_ILN2_HI")) << 64) | hexint(macro("PW_ILN2_LO")) == iln2
+    assert hexint(macro("PW_LN2")) == ln2
 
     def const(name):
         return float.fromhex(macro(name).rstrip("f"))
@@ -454,6 +452,73 @@ def test_pow_constants_are_correctly_rounded():
         assert hi == float(np.float32(float(c))) or abs(mpmath.mpf(hi) - c) <= mpmath.mpf(2) ** -25
         assert np.float32(hi) == hi and np.float32(lo) == lo
         assert abs(mpmath.mpf(hi) + lo - c) < mpmath.mpf(2) ** -47
+
+
+def _pow_table_definitions():
+    """The binary64 pow's tables from their definitions, at 400 bits:
+    C_j (the reference significand of the top 8 fraction bits j), R_j =
+    RN(2^179 / C_j), T_j = RN(log2(F_j) 2^80), TE_i = RN(2^(i/64) 2^63)."""
+    with mpmath.workprec(400):
+        two = mpmath.mpf(2)
+        rn = lambda v: int(mpmath.floor(v + mpmath.mpf("0.5")))
+        C = [(1 << 52) + ((j + (1 if j >= 128 else 0)) << 44) for j in range(256)]
+        R = [rn(two ** 179 / C[j]) for j in range(256)]
+        T = [rn(mpmath.log(mpmath.mpf(C[j]) / two ** (53 if j >= 128 else 52), 2) * two ** 80) for j in range(256)]
+        TE = [rn(two ** (mpmath.mpf(i) / 64) * two ** 63) for i in range(64)]
+    return C, R, T, TE
+
+
+def _oracle_pow_tables():
+    import ctypes
+    L = oracle.lib()
+    f = L.or_pow_tables_d
+    f.restype = None
+    f.argtypes = [ctypes.c_void_p] * 3
+    Ro, To, TEo = np.zeros(512, np.uint64), np.zeros(512, np.uint64), np.zeros(64, np.uint64)
+    f(Ro.ctypes.data, To.ctypes.data, TEo.ctypes.data)
+    R = [int(Ro[2 * j]) << 64 | int(Ro[2 * j + 1]) for j in range(256)]
+    T = [(int(To[2 * j]) << 64 | int(To[2 * j + 1])) - ((1 << 128) if int(To[2 * j]) >> 63 else 0) for j in range(256)]
+    return R, T, [int(v) for v in TEo]
+
+
+def test_pow_tables_match_their_definitions():
+    """The oracle builds the binary64 pow's tables itself (exact long
+    division for R_j, binary128 log2 and pow for T_j and TE_i); every entry
+    equals the 400-bit value rounded to nearest.  F_0 = F_255 = 1, so
+    T_0 = T_255 = 0: no cancellation next to x = 1."""
+    C, R, T, TE = _pow_table_definitions()
+    Ro, To, TEo = _oracle_pow_tables()
+    assert Ro == R and To == T and TEo == TE
+    assert T[0] == 0 and T[255] == 0 and R[0] == 1 << 127 and TE[0] == 1 << 63
+
+
+def test_kernel_pow_tables_match_the_definitions():
+    """The kernels' copy of the tables (paper_2509_06220_gb300/csrc/
+    nrm_pow_tables.h, written by gen_pow_tables.py beside it) holds the same
+    values as the definitions, and its constants 2^127/ln 2 and 2^64 ln 2."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2509_06220_gb300",
+                        "csrc", "nrm_pow_tables.h")
+    src = open(path).read()
+
+    def block(name):
+        body = src[src.index(name):]
+        body = body[body.index("{") + 1:body.index("};")]
+        return [int(v, 16) for v in re.findall(r"0x([0-9a-f]+)ull", body)]
+
+    C, R, T, TE = _pow_table_definitions()
+    r = block("kPowR[256][2]")
+    t = block("kPowT[256][2]")
+    te = block("kPowTE[64]")
+    assert [r[2 * j] << 64 | r[2 * j + 1] for j in range(256)] == R
+    assert [(t[2 * j] << 64 | t[2 * j + 1]) - ((1 << 128) if t[2 * j] >> 63 else 0) for j in range(256)] == T
+    assert te == TE
+    with mpmath.workprec(400):
+        iln2 = int(mpmath.floor(mpmath.mpf(2) ** 127 / mpmath.log(2) + mpmath.mpf("0.5")))
+        ln2 = int(mpmath.floor(mpmath.log(2) * mpmath.mpf(2) ** 64 + mpmath.mpf("0.5")))
+    const = lambda name: int(re.search(r"%s = 0x([0-9a-f]+)ull" % name, src).group(1), 16)
+    assert (const("kPowILN2_HI") << 64 | const("kPowILN2_LO")) == iln2 and const("kPowLN2") == ln2
 
 
 def _bits_d(v):
