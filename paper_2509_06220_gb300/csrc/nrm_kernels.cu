@@ -100,6 +100,20 @@ __device__ __forceinline__ void load_slot(const T *src, T (&r)[Geo<T>::V]) {
 // sweep on GB300 found 64 registers best for v1_hypot in both precisions).
 // FinalA: reduce the P lane partials with the correctly rounded hypot (the
 // algorithm A; Z with A is the paper's recommended xNRMF) instead of op.
+// stages of the cp.async ring of full items (Op::kStages, default none)
+template <class Op, class = void> struct StagesOf {
+    static constexpr int value = 0;
+};
+template <class Op> struct StagesOf<Op, std::void_t<decltype(Op::kStages)>> {
+    static constexpr int value = Op::kStages;
+};
+
+// dynamic shared memory of a tree block: per warp, the counter stack of MAXL
+// rows and the ring of StagesOf<Op> groups of 2^G rows (512 bytes a row)
+template <int G, class Op> constexpr size_t tree_smem_bytes(int wpb) {
+    return (size_t)wpb * ((size_t)MAXL * 512 + (size_t)StagesOf<Op>::value * (1u << G) * 512);
+}
+
 template <typename T, int G, class Op, bool FinalA = false>
 __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
     constexpr int V = Geo<T>::V;
@@ -111,6 +125,9 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
     const int64_t total = batch ? *a.total_items : a.item_hi;
     extern __shared__ __align__(16) unsigned char nrm_smem[];
     T *stk = reinterpret_cast<T *>(nrm_smem) + (threadIdx.x >> 5) * (MAXL * P);
+    constexpr int NS = StagesOf<Op>::value;
+    typename Geo<T>::vec *ring = reinterpret_cast<typename Geo<T>::vec *>(
+        nrm_smem + (size_t)(blockDim.x >> 5) * MAXL * 512 + (size_t)(threadIdx.x >> 5) * (NS * (1u << G) * 512));
 
     int64_t gi;
     if (batch) {
@@ -142,7 +159,12 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
         const int64_t t = node_rows(pl.m, i, pl.dw);
         const int64_t start = node_start(pl.m, i, pl.dw);
         T r[V];
-        item_tree<T, G, Op>(xv, pl.n, start, t, pl.k, lane, aligned, pl.stride, op, stk, r);
+        bool done = false;
+        if constexpr (NS > 0) {
+            if (aligned && pl.k > G && t == (int64_t(1) << pl.k) && (start + t) * P <= pl.n)
+                done = item_tree_async<T, G, Op, NS>(xv, start, pl.k, lane, op, stk, ring, r);
+        }
+        if (!done) item_tree<T, G, Op>(xv, pl.n, start, t, pl.k, lane, aligned, pl.stride, op, stk, r);
 
         // climb the ticket tree above the cut
         uint32_t h = (1u << pl.dw) + i;
@@ -520,13 +542,13 @@ static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, i
                                cudaStream_t s) {
     const nrm_tuning &tu = tune_of<T>(c);
     const int wpb = tu.warps_per_block;
-    const size_t smem = (size_t)wpb * MAXL * 512; // per-warp counter stacks
     int occ = 0;
     int64_t blocks = 0;
     cudaError_t e = cudaSuccess;
     switch (tu.group_log2) {
 #define NRM_LAUNCH_G(GG)                                                                                    \
     case GG: {                                                                                              \
+        const size_t smem = tree_smem_bytes<GG, Op>(wpb);                                                  \
         cudaFuncSetAttribute(tree_kernel<T, GG, Op, FinalA>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                              (int)smem);                                                                    \
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<T, GG, Op, FinalA>, wpb * 32, smem); \
@@ -852,7 +874,7 @@ nrm_status na_setup(int dev, NaDevice **out) {
         e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return NRM_ECUDA;
         int occ = 0;
-        const size_t smem = (size_t)NA_WPB * MAXL * 512;
+        const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<double, NA_G, OpHypot<double>>,
                                                           NA_WPB * 32, smem);
         if (e != cudaSuccess) return NRM_ECUDA;
@@ -907,7 +929,7 @@ extern "C" nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, vo
     a.item_hi = items;
     a.tickets = tickets;
     a.slots = slots;
-    const size_t smem = (size_t)NA_WPB * MAXL * 512;
+    const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + NA_WPB - 1) / NA_WPB,
                                                                   (int64_t)d->sms * d->occ));
     tree_kernel<double, NA_G, OpHypot<double>><<<(unsigned)blocks, NA_WPB * 32, smem, s>>>(a, OpHypot<double>{});
