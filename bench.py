@@ -45,8 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the ncu traffic figures in profiles/ belong to the kernel build they were
 # captured on; set to False whenever the binary64 tree kernel changes
 TRAFFIC_VALID = True
-TRAFFIC_D_2E28 = 2147.770e6 + 10.934272e6  # DNRMF: DRAM read + write of one launch at n = 2^28
-TRAFFIC_S_2E28 = 1073.890e6 + 7.412224e6  # SNRMF: the same
+TRAFFIC_D_2E28 = 2151.303e6 + 36.16256e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1073.889e6 + 7.24736e6  # SNRMF: the same
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

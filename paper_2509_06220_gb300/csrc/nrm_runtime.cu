@@ -248,7 +248,7 @@ extern "C" nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t 
     for (int G = 2; G <= 3 && st == NRM_OK; ++G)
         for (int wpb : {4, 8, 16})
             for (int k = G + 3; k <= G + 6 && st == NRM_OK; ++k)
-                for (int bps : {2, 4, 8}) {
+                for (int bps : {2, 4, 8, 16}) {
                     ctx->tune[dtype] = nrm_tuning{G, wpb, k, bps};
                     if (total == 0) break;
                     st = run(); // warm-up (and workspace growth)
