@@ -229,7 +229,7 @@ def time_serving(nrm, seconds, rate):
     import numpy as np
     tr = nrm.serving_trace(rate, seconds, seed=0)
     res, norms = {}, {}
-    for name, (ns, mb) in (("batched", (2, 1024)), ("one_request_per_launch", (1, 1))):
+    for name, (ns, mb) in (("batched", (4, 256)), ("one_request_per_launch", (1, 1))):
         srv = nrm.Server(budget_bytes=8 << 30, nstreams=ns, max_batch=mb)
         v, lat, rep = srv.replay(tr)
         srv.close()
