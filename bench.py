@@ -363,6 +363,24 @@ def main():
                                 "hbm_frac": s_bytes_gbs / hbm_peak,
                                 "traffic": TRAFFIC_S_2E28 * (N / float(1 << 28)) if TRAFFIC_VALID else None}}}
 
+    # the other hypot variants on the same vectors (not the headline): Z with
+    # A for the final reduction, and the exponent-scaled hypotenuse K2
+    if rank == 0 and not args.no_batch:
+        variants = {}
+        for name, fn in (("za", nrm.nrmf_za), ("es", nrm.nrmf_es)):
+            for tag, x, o in (("d", xd, od), ("s", xs, os_)):
+                fn(x, out=o, ctx=ctx)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(5):
+                    fn(x, out=o, ctx=ctx)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 5
+                variants["%snrmf_%s" % (tag, name)] = {"ms": ms, "GBps": N * x.element_size() / (ms * 1e-3) / 1e9}
+        line["parts"]["variants"] = variants
+
     # end to end through the host-buffer entry point
     if not args.no_e2e:
         hd = torch.empty(N, dtype=torch.float64, pin_memory=True)

@@ -140,6 +140,23 @@ nrm_status nrmf_za_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *
 nrm_status nrmf_za_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream);
 
 /*
+ * xNRMF with another hypot[f] (Section 2 admits any hypotenuse that avoids
+ * undue overflow and underflow, is monotone in |x| and |y| and accurate to a
+ * small multiple of eps): the exponent-scaled hypotenuse K2 in place of
+ * v1_hypot in the whole tree (Z and the final reduction R of Section 3).
+ * With m = min(|x|,|y|), M = max (a NaN operand is missing data) and k the
+ * binade of M (the lowest normal binade for a subnormal M):
+ *   a = M 2^-k, b = RN(m 2^-k), S = RN(fma(a, a, RN(b b))), s = RN(sqrt(S)),
+ *   K2 = RN(s 2^k);  K2 = +0 for M = 0 and +inf for M = inf.
+ * No division; relative error at most 1.75 eps + O(eps^2) per combine
+ * without underflow; K2(a, 0) = |a| exactly.  A different set of bits from
+ * nrmf_* (another hypot), bitwise reproducible and equal to the oracle's
+ * or_nrm_es_*.  Arguments and errors as nrmf_*.
+ */
+nrm_status nrmf_es_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *stream);
+nrm_status nrmf_es_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream);
+
+/*
  * xNRMP (Section 4): *out = ||x[0..n)||_p by the same tree with the combine
  * chosen by p: p == 2 is exactly xNRMF; p == 1 sums |x| (Eq. vp1); p == +inf
  * takes max |x| (Eq. vpI); otherwise v1_lp (Listing 5, Eqs. sp and qp) with
@@ -394,6 +411,24 @@ nrm_status nrm_test_combine(nrm_dtype dtype, double p, const void *x, const void
  * or null pointers. */
 nrm_status nrm_test_k1f_exhaustive(int32_t mode, uint64_t start, uint64_t count, unsigned long long *bad,
                                    float *example, void *stream);
+/* (mode 3 of nrm_test_k1f_exhaustive: the same square root on the 3 2^23
+ * values S in [1, 8), index i: S = (1 + (i mod 2^23) 2^-23) 2^(i / 2^23),
+ * the range K2's binary32 form uses.) */
+
+/* Test hook: K2 (see nrmf_es_*) elementwise in the general form the trees
+ * use outside checked groups: out[i] = K2(x[i], y[i]) on device arrays of n
+ * elements of `dtype`.  Asynchronous; NRM_EINVAL for n < 0, null arrays or
+ * an unknown dtype. */
+nrm_status nrm_test_k2(nrm_dtype dtype, const void *x, const void *y, void *out, int64_t n, void *stream);
+
+/* Test hook: the branch-free binary64 K2 of the checked groups (integer
+ * square root, exact scalings) against the general form (FP64 square root)
+ * on n operand pairs of family `mode` (the families of
+ * nrm_test_k1d_compare), for the pairs inside its range [2^-500, 2^502);
+ * bitwise differences are added to *bad and one of them stored in
+ * example[0..3] (x, y, both results; device pointers).  Asynchronous. */
+nrm_status nrm_test_k2d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad, double *example,
+                                void *stream);
 
 /* Test hook: copy the first `count` ticket counters of the context's
  * workspace to host memory (synchronous).  Between calls they are all zero. */

@@ -40,6 +40,12 @@ def lib():
             "or_lp_arr_d": (None, [i64, d, d, vp, vp, vp]),
             "or_lp_arr_s": (None, [i64, f, f, vp, vp, vp]),
             "or_comb_arr_d": (None, [i64, d, vp, vp, vp]),
+            "or_k2_d": (d, [d, d]),
+            "or_k2_s": (f, [f, f]),
+            "or_k2_arr_d": (None, [i64, vp, vp, vp]),
+            "or_k2_arr_s": (None, [i64, vp, vp, vp]),
+            "or_nrm_es_d": (d, [i64, vp, i32]),
+            "or_nrm_es_s": (f, [i64, vp, i32]),
             "or_comb_arr_s": (None, [i64, f, vp, vp, vp]),
             "or_R_d": (d, [i64, vp, d]),
             "or_R_s": (f, [i64, vp, f]),
@@ -131,6 +137,33 @@ def comb_arr(p, x, y):
     f = lib().or_comb_arr_d if dt == np.float64 else lib().or_comb_arr_s
     f(xa.size, float(p) if dt == np.float64 else float(np.float32(p)), xp, yp, out.ctypes.data_as(ctypes.c_void_p))
     return out
+
+
+def k2(x, y, dtype=np.float64):
+    """The exponent-scaled hypotenuse K2 (binary64 or binary32)."""
+    if np.dtype(dtype) == np.float64:
+        return np.float64(lib().or_k2_d(float(x), float(y)))
+    return np.float32(lib().or_k2_s(float(np.float32(x)), float(np.float32(y))))
+
+
+def k2_arr(x, y):
+    """Elementwise K2 over two arrays of one dtype."""
+    dt = np.asarray(x).dtype
+    xa, xp = _arr(x, dt)
+    ya, yp = _arr(y, dt)
+    out = np.empty(xa.shape, dt)
+    f = lib().or_k2_arr_d if dt == np.float64 else lib().or_k2_arr_s
+    f(xa.size, xp, yp, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def nrm_es(x):
+    """xNRMF with K2 in place of v1_hypot (same tree, P = 64 / 128)."""
+    dt = np.asarray(x).dtype
+    a, ap = _arr(x, dt)
+    if dt == np.float64:
+        return np.float64(lib().or_nrm_es_d(a.size, ap, P_D))
+    return np.float32(lib().or_nrm_es_s(a.size, ap, P_S))
 
 
 def lp(p, x, y, dtype=np.float64):

@@ -33,6 +33,9 @@
  *                          (Section 2), from its definition with integers
  *   or_nrm_za_*            Z then A for the final reduction (Section 3's
  *                          recommendation for xNRMF)
+ *   or_k2_* / or_nrm_es_*  the exponent-scaled hypotenuse K2 (a division-
+ *                          free hypot[f] admitted by Section 2) and xNRMF
+ *                          with it in place of v1_hypot
  *   or_nrm_strided_*       a strided vector (BLAS incx, Section 3)
  *   or_nrm_matrix_*        a matrix with a leading dimension (Section 3.1)
  *   or_nrm_slot_*          the same tree evaluated in "slot form" (a perfect
@@ -83,7 +86,7 @@ static inline uint32_t bits_s(float x);
 static inline float from_bits_s(uint32_t u);
 
 /* Combine op selector: which per-node operation the tree applies. */
-enum { OP_HYPOT = 0, OP_LP = 1, OP_SUMABS = 2, OP_MAXABS = 3 };
+enum { OP_HYPOT = 0, OP_LP = 1, OP_SUMABS = 2, OP_MAXABS = 3, OP_K2 = 4 };
 
 /* fmin / fmax of Listings 2 and 5 with C's Annex F rule written out: a NaN
  * argument counts as missing data and the other one is returned.  The rule
@@ -124,6 +127,69 @@ OR_API float or_k1_s(float x, float y)
     const float S = fmaf(Q, Q, 1.0f);
     const float s = sqrtf(S);
     return M * s;
+}
+
+/* 2^e as a double (binary32: a float) for e in [-1074, 1023] ([-149, 127]),
+ * built from its bit pattern. */
+static double p2_d(int e)
+{
+    if (e >= -1022) return from_bits_d((uint64_t)(e + 1023) << 52);
+    return from_bits_d(1ull << (e + 1074));
+}
+
+static float p2_s(int e)
+{
+    if (e >= -126) return from_bits_s((uint32_t)(e + 127) << 23);
+    return from_bits_s(1u << (e + 149));
+}
+
+/*
+ * K2: the exponent-scaled hypotenuse, a division-free hypot[f] for the tree
+ * (Section 2 admits any hypot that avoids undue overflow and underflow, is
+ * monotone in |x| and |y| and accurate to a small multiple of eps; this is
+ * the variant the scope lists next to A).  With m = min(|x|,|y|), M = max
+ * (a NaN is missing data, as in v1_hypot) and k the binade of M (k = emin
+ * for a subnormal M):
+ *   a = M 2^-k (exact), b = RN(m 2^-k), S = RN(fma(a, a, RN(b b))),
+ *   s = RN(sqrt(S)), K2 = RN(s 2^k);
+ * M = 0 gives +0, M = inf gives +inf, two NaNs give a NaN.  Each step is one
+ * IEEE operation rounded to nearest; K2(a, 0) = |a| exactly (sqrt(RN(a^2))
+ * = |a|), and the relative error is at most 1.75 eps + O(eps^2) when nothing
+ * underflows (b b contributes eps b^2/S <= eps/2 to S, the fma eps, their
+ * square root half of it, and the root itself eps).
+ */
+OR_API double or_k2_d(double x, double y)
+{
+    const double X = fabs(x);
+    const double Y = fabs(y);
+    const double m = min_d(X, Y);
+    const double M = max_d(X, Y);
+    if (isnan(M)) return M;
+    if (M == 0.0) return 0.0;
+    if (isinf(M)) return M;
+    const int k = M < 0x1p-1022 ? -1022 : ilogb(M);
+    const double a = M * p2_d(-k);
+    const double b = m * p2_d(-k);
+    const double S = fma(a, a, b * b);
+    const double s = sqrt(S);
+    return s * p2_d(k);
+}
+
+OR_API float or_k2_s(float x, float y)
+{
+    const float X = fabsf(x);
+    const float Y = fabsf(y);
+    const float m = min_s(X, Y);
+    const float M = max_s(X, Y);
+    if (isnan(M)) return M;
+    if (M == 0.0f) return 0.0f;
+    if (isinf(M)) return M;
+    const int k = M < 0x1p-126f ? -126 : ilogbf(M);
+    const float a = M * p2_s(-k);
+    const float b = m * p2_s(-k);
+    const float S = fmaf(a, a, b * b);
+    const float s = sqrtf(S);
+    return s * p2_s(k);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -675,6 +741,7 @@ static double comb_apply_d(const comb_d *c, double x, double y)
 {
     switch (c->op) {
     case OP_HYPOT: return or_k1_d(x, y);
+    case OP_K2: return or_k2_d(x, y);
     case OP_LP: return or_lp_d(c->h, c->ip, x, y);
     case OP_SUMABS: return sumabs_d(x, y);
     default: return maxabs_d(x, y);
@@ -685,6 +752,7 @@ static float comb_apply_s(const comb_s *c, float x, float y)
 {
     switch (c->op) {
     case OP_HYPOT: return or_k1_s(x, y);
+    case OP_K2: return or_k2_s(x, y);
     case OP_LP: return or_lp_s(c->h, c->ip, x, y);
     case OP_SUMABS: return sumabs_s(x, y);
     default: return maxabs_s(x, y);
@@ -945,6 +1013,41 @@ OR_API float or_nrm_za_s(int64_t n, const float *x, int P)
     const float v = R_cr_s(P, f);
     free(f);
     return v;
+}
+
+/* xNRMF with the exponent-scaled hypotenuse K2 in place of v1_hypot
+ * everywhere: the same tree Z and final reduction R (Section 3), another
+ * hypot[f] (Section 2). */
+OR_API double or_nrm_es_d(int64_t n, const double *x, int P)
+{
+    if (n <= 0) return 0.0;
+    const comb_d c = {OP_K2, 0.0, 0.0};
+    double *f = (double *)malloc(sizeof(double) * (size_t)P);
+    Z_d(n, x, P, &c, f);
+    const double v = R_d(P, f, &c);
+    free(f);
+    return v;
+}
+
+OR_API float or_nrm_es_s(int64_t n, const float *x, int P)
+{
+    if (n <= 0) return 0.0f;
+    const comb_s c = {OP_K2, 0.0f, 0.0f};
+    float *f = (float *)malloc(sizeof(float) * (size_t)P);
+    Z_s(n, x, P, &c, f);
+    const float v = R_s(P, f, &c);
+    free(f);
+    return v;
+}
+
+OR_API void or_k2_arr_d(int64_t n, const double *x, const double *y, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_k2_d(x[i], y[i]);
+}
+
+OR_API void or_k2_arr_s(int64_t n, const float *x, const float *y, float *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_k2_s(x[i], y[i]);
 }
 
 /* Batched form: out[i] = or_nrm of x[off[i] .. off[i+1]). */

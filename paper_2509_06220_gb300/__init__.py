@@ -93,6 +93,8 @@ def load():
         "nrmp_s": (st, [vp, vp, i64, ctypes.c_float, vp, vp]),
         "nrmf_za_s": (st, [vp, vp, i64, vp, vp]),
         "nrmf_za_d": (st, [vp, vp, i64, vp, vp]),
+        "nrmf_es_s": (st, [vp, vp, i64, vp, vp]),
+        "nrmf_es_d": (st, [vp, vp, i64, vp, vp]),
         "nrmp_d": (st, [vp, vp, i64, ctypes.c_double, vp, vp]),
         "nrm_batch": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, vp]),
         "nrm_batch_graph": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, ctypes.POINTER(vp)]),
@@ -279,6 +281,21 @@ def nrmp(x, p=2.0, out=None, stream=None, ctx=None):
 def nrmf(x, out=None, stream=None, ctx=None):
     """xNRMF: the Frobenius norm by the recursive v1_hypot tree."""
     return nrmp(x, 2.0, out, stream, ctx)
+
+
+def nrmf_es(x, out=None, stream=None, ctx=None):
+    """xNRMF with the exponent-scaled hypotenuse K2 (no division) in place of
+    v1_hypot throughout the tree: another hypot[f] of Section 2."""
+    import torch
+    _check_vec(x)
+    dt = _dtype_code(x)
+    c = ctx or context(x.device)
+    if out is None:
+        out = torch.empty((), dtype=x.dtype, device=x.device)
+    f = load().nrmf_es_d if dt == NRM_F64 else load().nrmf_es_s
+    c.check(f(c.h, ctypes.c_void_p(x.data_ptr() if x.numel() else 0), x.numel(), ctypes.c_void_p(out.data_ptr()),
+              _stream(stream)), "nrmf_es")
+    return out
 
 
 def nrmf_za(x, out=None, stream=None, ctx=None):

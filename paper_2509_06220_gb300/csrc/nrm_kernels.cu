@@ -585,7 +585,7 @@ template <typename T, class F> static cudaError_t with_op(T p, F &&f) {
 
 template <typename T>
 static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cudaStream_t s, int64_t item_lo,
-                             int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1, bool final_a = false) {
+                             int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1, int variant = 0) {
     VecPlan pl;
     if (plan_in) pl = *plan_in;
     else if (!plan_single(c, n, P_of<T>(), pl)) return NRM_EINVAL;
@@ -609,7 +609,10 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
     a.slots = reinterpret_cast<T *>((char *)c->ws + L.slots);
     const int64_t warps = a.item_hi - a.item_lo;
     cudaError_t e;
-    if (final_a) e = launch_tree<T, OpHypot<T>, true>(c, a, OpHypot<T>{}, warps, s);
+    // variant 0: the combine of p; 1: Z with A (cr_hypot for the lane
+    // reduction); 2: the exponent-scaled hypotenuse K2 throughout
+    if (variant == 1) e = launch_tree<T, OpHypot<T>, true>(c, a, OpHypot<T>{}, warps, s);
+    else if (variant == 2) e = launch_tree<T, OpHypot2<T>>(c, a, OpHypot2<T>{}, warps, s);
     else e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, warps, s); });
     return set_cuda_err(c, e, "tree_kernel launch");
 }
@@ -651,7 +654,23 @@ template <typename T> static nrm_status za_entry(nrm_ctx *c, const T *x, int64_t
     if (st != NRM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (n == 0) return set_cuda_err(c, cudaMemsetAsync(out, 0, sizeof(T), s), "cudaMemsetAsync");
-    return run_single<T>(c, x, n, T(2), out, s, 0, 0, nullptr, 1, true);
+    return run_single<T>(c, x, n, T(2), out, s, 0, 0, nullptr, 1, 1);
+}
+
+// xNRMF with the exponent-scaled hypotenuse K2 (a hypot[f] variant, Section 2)
+template <typename T> static nrm_status es_entry(nrm_ctx *c, const T *x, int64_t n, T *out, void *stream) {
+    nrm_status st = check_args<T>(c, x, n, T(2), out);
+    if (st != NRM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return set_cuda_err(c, cudaMemsetAsync(out, 0, sizeof(T), s), "cudaMemsetAsync");
+    return run_single<T>(c, x, n, T(2), out, s, 0, 0, nullptr, 1, 2);
+}
+
+extern "C" nrm_status nrmf_es_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *stream) {
+    return es_entry<float>(ctx, x, n, out, stream);
+}
+extern "C" nrm_status nrmf_es_d(nrm_ctx *ctx, const double *x, int64_t n, double *out, void *stream) {
+    return es_entry<double>(ctx, x, n, out, stream);
 }
 
 extern "C" nrm_status nrmf_za_s(nrm_ctx *ctx, const float *x, int64_t n, float *out, void *stream) {
@@ -966,55 +985,61 @@ __device__ __forceinline__ uint64_t th_frac(uint64_t u, int kind) {
     }
 }
 
+// operand pair i of family `mode` for the compare tests (see
+// nrm_test_k1d_compare in include/nrm.h for the families)
+__device__ __forceinline__ void k1d_pair(uint64_t seed, int64_t i, int mode, double &x, double &y) {
+    const uint64_t u1 = th_mix(seed + (uint64_t)(4 * i + 1) * 0x9E3779B97F4A7C15ull);
+    const uint64_t u2 = th_mix(seed + (uint64_t)(4 * i + 2) * 0x9E3779B97F4A7C15ull);
+    const uint64_t u3 = th_mix(seed + (uint64_t)(4 * i + 3) * 0x9E3779B97F4A7C15ull);
+    const int64_t e1 = 1023 - 40 + (int64_t)(u3 % 81);
+    switch (mode) {
+    case 0: { // moderate: exponent gap 0..32
+        const int64_t dd = (int64_t)((u3 >> 20) % 33);
+        x = th_make(u1 >> 63, e1, u1);
+        y = th_make(u2 >> 63, e1 - dd, u2);
+        break;
+    }
+    case 1: { // close values: gap -1, 0, +1
+        const int64_t dd = (int64_t)((u3 >> 20) % 3) - 1;
+        x = th_make(u1 >> 63, e1, u1);
+        y = th_make(u2 >> 63, e1 + dd, ((u3 >> 30) & 1) ? (u1 + ((u2 >> 40) - (1ull << 23))) : u2);
+        break;
+    }
+    case 2: { // edge significands, gap 0..30
+        const int64_t dd = (int64_t)((u3 >> 20) % 31);
+        x = th_make(u1 >> 63, e1, th_frac(u1, (int)(u3 >> 40)));
+        y = th_make(u2 >> 63, e1 - dd, th_frac(u2, (int)(u3 >> 44)));
+        break;
+    }
+    case 3: // raw bit patterns: every class (inf, NaN, subnormal, zero, extremes)
+        x = __longlong_as_double((long long)u1);
+        y = __longlong_as_double((long long)(((u3 >> 10) & 1) ? u2 : (u1 ^ (u2 & 0xffffull))));
+        break;
+    case 4: { // extremes: near the largest and the smallest normal exponent
+        const int64_t ex = ((u3 >> 9) & 1) ? 2046 - (int64_t)((u3 >> 12) % 4) : 1 + (int64_t)((u3 >> 12) % 4);
+        const int64_t dd = (int64_t)((u3 >> 20) % 31);
+        x = th_make(0, ex, u1);
+        y = th_make(0, ex - dd > 0 ? ex - dd : 0, u2);
+        break;
+    }
+    case 5: { // gaps around the S = 1 shortcut
+        const int64_t dd = 25 + (int64_t)((u3 >> 20) % 5);
+        x = th_make(0, e1, th_frac(u1, (int)(u3 >> 40)));
+        y = th_make(0, e1 - dd, th_frac(u2, (int)(u3 >> 44)));
+        break;
+    }
+    default: { // equal or nearly equal values (S near 2)
+        x = th_make(0, e1, u1);
+        y = th_make(0, e1, u1 - (u2 & 0x3ff) + ((u2 >> 12) & 0x3ff));
+        break;
+    }
+    }
+}
+
 __global__ void k1d_compare_kernel(uint64_t seed, int64_t n, int mode, unsigned long long *bad, double *example) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t u1 = th_mix(seed + (uint64_t)(4 * i + 1) * 0x9E3779B97F4A7C15ull);
-        const uint64_t u2 = th_mix(seed + (uint64_t)(4 * i + 2) * 0x9E3779B97F4A7C15ull);
-        const uint64_t u3 = th_mix(seed + (uint64_t)(4 * i + 3) * 0x9E3779B97F4A7C15ull);
         double x, y;
-        const int64_t e1 = 1023 - 40 + (int64_t)(u3 % 81);
-        switch (mode) {
-        case 0: { // moderate: exponent gap 0..32
-            const int64_t dd = (int64_t)((u3 >> 20) % 33);
-            x = th_make(u1 >> 63, e1, u1);
-            y = th_make(u2 >> 63, e1 - dd, u2);
-            break;
-        }
-        case 1: { // close values: gap -1, 0, +1
-            const int64_t dd = (int64_t)((u3 >> 20) % 3) - 1;
-            x = th_make(u1 >> 63, e1, u1);
-            y = th_make(u2 >> 63, e1 + dd, ((u3 >> 30) & 1) ? (u1 + ((u2 >> 40) - (1ull << 23))) : u2);
-            break;
-        }
-        case 2: { // edge significands, gap 0..30
-            const int64_t dd = (int64_t)((u3 >> 20) % 31);
-            x = th_make(u1 >> 63, e1, th_frac(u1, (int)(u3 >> 40)));
-            y = th_make(u2 >> 63, e1 - dd, th_frac(u2, (int)(u3 >> 44)));
-            break;
-        }
-        case 3: // raw bit patterns: every class (inf, NaN, subnormal, zero, extremes)
-            x = __longlong_as_double((long long)u1);
-            y = __longlong_as_double((long long)(((u3 >> 10) & 1) ? u2 : (u1 ^ (u2 & 0xffffull))));
-            break;
-        case 4: { // extremes: near the largest and the smallest normal exponent
-            const int64_t ex = ((u3 >> 9) & 1) ? 2046 - (int64_t)((u3 >> 12) % 4) : 1 + (int64_t)((u3 >> 12) % 4);
-            const int64_t dd = (int64_t)((u3 >> 20) % 31);
-            x = th_make(0, ex, u1);
-            y = th_make(0, ex - dd > 0 ? ex - dd : 0, u2);
-            break;
-        }
-        case 5: { // gaps around the S = 1 shortcut
-            const int64_t dd = 25 + (int64_t)((u3 >> 20) % 5);
-            x = th_make(0, e1, th_frac(u1, (int)(u3 >> 40)));
-            y = th_make(0, e1 - dd, th_frac(u2, (int)(u3 >> 44)));
-            break;
-        }
-        default: { // equal or nearly equal values (S near 2)
-            x = th_make(0, e1, u1);
-            y = th_make(0, e1, u1 - (u2 & 0x3ff) + ((u2 >> 12) & 0x3ff));
-            break;
-        }
-        }
+        k1d_pair(seed, i, mode, x, y);
         const double a = k1_exact(x, y), b = k1(x, y);
         const bool same = (__double_as_longlong(a) == __double_as_longlong(b)) || (isnan(a) && isnan(b));
         if (!same) {
@@ -1082,6 +1107,24 @@ extern "C" nrm_status nrm_test_combine(nrm_dtype dtype, double p, const void *x,
     return e == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }
 
+template <typename T> __global__ void k2_eval_kernel(const T *x, const T *y, T *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = k2(x[i], y[i]);
+}
+
+extern "C" nrm_status nrm_test_k2(nrm_dtype dtype, const void *x, const void *y, void *out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !y || !out)) || (dtype != NRM_F64 && dtype != NRM_F32)) return NRM_EINVAL;
+    if (n == 0) return NRM_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (dtype == NRM_F64)
+        k2_eval_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>((const double *)x, (const double *)y,
+                                                                      (double *)out, n);
+    else
+        k2_eval_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>((const float *)x, (const float *)y,
+                                                                     (float *)out, n);
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
+
 extern "C" nrm_status nrm_test_lp(nrm_dtype dtype, double p, const void *x, const void *y, void *out, int64_t n,
                                   void *stream) {
     if (n < 0 || (n > 0 && (!x || !y || !out)) || !(p > 0.0) || (dtype != NRM_F64 && dtype != NRM_F32))
@@ -1121,8 +1164,8 @@ __global__ void k1f_exhaustive_kernel(int mode, uint64_t start, uint64_t count, 
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i = start + t;
-        if (mode == 0) {
-            if (i > (1ull << 23)) continue;
+        if (mode == 0 || mode == 3) {
+            if (i > (mode == 0 ? (1ull << 23) : 3 * (1ull << 23) - 1)) continue;
             const float S = __uint_as_float(0x3f800000u + (uint32_t)i);
             if (__float_as_uint(sqrtf_fast(S)) != __float_as_uint(__fsqrt_rn(S))) {
                 ++nb;
@@ -1160,9 +1203,39 @@ __global__ void k1f_exhaustive_kernel(int mode, uint64_t start, uint64_t count, 
 
 extern "C" nrm_status nrm_test_k1f_exhaustive(int32_t mode, uint64_t start, uint64_t count, unsigned long long *bad,
                                               float *example, void *stream) {
-    if (mode < 0 || mode > 2 || !bad || !example) return NRM_EINVAL;
+    if (mode < 0 || mode > 3 || !bad || !example) return NRM_EINVAL;
     if (count == 0) return NRM_OK;
     k1f_exhaustive_kernel<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(mode, start, count, bad, example);
+    return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
+}
+
+// k2_exact_fast against k2 (FP64 square root) on the k1d_compare families,
+// for pairs inside the fast form's range [2^-500, 2^502) (others skipped).
+__global__ void k2d_compare_kernel(uint64_t seed, int64_t n, int mode, unsigned long long *bad, double *example) {
+    unsigned long long nb = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double x, y;
+        k1d_pair(seed, i, mode, x, y);
+        const uint32_t hx = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32) & 0x7fffffffu;
+        const uint32_t hy = (uint32_t)((uint64_t)__double_as_longlong(y) >> 32) & 0x7fffffffu;
+        const uint32_t lo = (uint32_t)(1023 - 500) << 20, hi = (uint32_t)(1023 + 502) << 20;
+        if (hx < lo || hx >= hi || hy < lo || hy >= hi) continue;
+        const double a = k2_exact_fast(x, y), b = k2(x, y);
+        if (__double_as_longlong(a) != __double_as_longlong(b)) {
+            ++nb;
+            example[0] = x;
+            example[1] = y;
+            example[2] = a;
+            example[3] = b;
+        }
+    }
+    if (nb) atomicAdd(bad, nb);
+}
+
+extern "C" nrm_status nrm_test_k2d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad,
+                                           double *example, void *stream) {
+    if (n < 0 || !bad || !example || mode < 0 || mode > 6) return NRM_EINVAL;
+    k2d_compare_kernel<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(seed, n, mode, bad, example);
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }
 

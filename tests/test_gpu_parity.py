@@ -700,14 +700,15 @@ def test_lp_combine_parity(nrm, dt, p):
     assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_k1f_fast_steps_exhaustive(nrm, mode):
     """The branch-free binary32 v1_hypot the S trees use on checked groups
     equals Listing 2's correctly rounded steps: its square root on every S in
     [1, 2] (mode 0), its division on every pair of significands (mode 2, all
     2^46 pairs), and the FP32 reciprocal estimate it starts from scales
     exactly with the exponent over the checked range (mode 1), so the pair
-    test covers every exponent there."""
+    test covers every exponent there; mode 3: the square root on every S in
+    [1, 8), the range of K2's binary32 form."""
     import ctypes
     L = nrm.load()
     f = L.nrm_test_k1f_exhaustive
@@ -715,7 +716,7 @@ def test_k1f_fast_steps_exhaustive(nrm, mode):
     f.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     bad = torch.zeros(1, dtype=torch.int64, device=DEV)
     ex = torch.zeros(2, dtype=torch.float32, device=DEV)
-    total = {0: (1 << 23) + 1, 1: 213 << 23, 2: 1 << 46}[mode]
+    total = {0: (1 << 23) + 1, 1: 213 << 23, 2: 1 << 46, 3: 3 << 23}[mode]
     chunk = 1 << 40
     for s in range(0, total, chunk):
         assert f(mode, s, min(chunk, total - s), ctypes.c_void_p(bad.data_ptr()), ctypes.c_void_p(ex.data_ptr()),
@@ -827,3 +828,84 @@ def test_combine_parity(nrm, dt, p):
     ui = np.uint64 if dt == np.float64 else np.uint32
     bad = ~((got.view(ui) == want.view(ui)) | (np.isnan(got) & np.isnan(want)))
     assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])
+
+
+# ---------------------------------------------------------------------------
+# the exponent-scaled hypotenuse K2 (nrmf_es_*)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_es_parity(nrm, dt):
+    """xNRMF with K2 equals the oracle's or_nrm_es bit for bit over sizes
+    with ragged tails, full items and several work items, on moderately and
+    widely varying data, with zeros, NaN pairs, inf and subnormals mixed in,
+    and on vectors straddling the checked range."""
+    rng = np.random.default_rng(50)
+    for n in (1, 2, 3, 127, 129, 4096, 100003, 3 * (1 << 20) + 17):
+        for emin, emax in ((-20, 20), (-8, 8), (-300, 300) if dt == np.float64 else (-60, 60)):
+            x = inputs.vector(n, seed=51, vec=n % 11, dtype=dt, emin=emin, emax=emax)
+            got = nrm.nrmf_es(dev(x)).cpu().numpy()
+            assert bits_equal(np.asarray(got, dt), np.asarray(oracle.nrm_es(x), dt)), (n, emin, emax)
+    n = 5 * (1 << 18) + 77
+    P = 128 if dt == np.float32 else 64
+    lo, hi = (-88, 118) if dt == np.float32 else (-500, 494)
+    for fam in range(5):
+        x = inputs.vector(n, seed=52 + fam, vec=1, dtype=dt)
+        pos = rng.choice(n - P, 64, replace=False)
+        with np.errstate(all="ignore"):
+            if fam == 0:
+                x[pos] = (2.0 ** rng.integers(lo - 4, lo + 4, 64)).astype(dt)
+            elif fam == 1:
+                x[pos] = (2.0 ** rng.integers(hi - 4, hi + 4, 64)).astype(dt)
+            elif fam == 2:
+                x[pos] = np.nan
+                x[pos + P] = np.nan
+            elif fam == 3:
+                x[pos[:3]] = np.inf
+                x[pos[3:20]] = 0
+            else:
+                x[pos] = (rng.integers(1, 1000, 64) * np.finfo(dt).smallest_subnormal).astype(dt)
+        got = nrm.nrmf_es(dev(x)).cpu().numpy()
+        assert bits_equal(np.asarray(got, dt), np.asarray(oracle.nrm_es(x), dt)), fam
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_k2_elementwise_parity(nrm, dt):
+    """The general K2 the trees use outside checked groups equals the
+    oracle's K2 bit for bit on 2^19 operand pairs (the combine families:
+    carries, ties, subnormals, overflow to inf, zeros, raw bit patterns)."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_k2
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    x, y = _combine_operands(dt, 1 << 19, seed=61)
+    xd, yd = dev(x), dev(y)
+    out = torch.empty_like(xd)
+    code = nrm.NRM_F64 if dt == np.float64 else nrm.NRM_F32
+    assert f(code, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+             x.size, None) == 0
+    got = out.cpu().numpy()
+    want = oracle.k2_arr(x, y)
+    ui = np.uint64 if dt == np.float64 else np.uint32
+    bad = ~((got.view(ui) == want.view(ui)) | (np.isnan(got) & np.isnan(want)))
+    assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 5, 6])
+def test_k2_fast_matches_general(nrm, mode):
+    """The checked-group binary64 K2 (integer square root for S in [1, 8),
+    exact scalings) equals the general form with the FP64 square root on
+    2^30 generated pairs per family inside its range."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_k2d_compare
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    bad = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ex = torch.zeros(4, dtype=torch.float64, device=DEV)
+    for rep in range(4):
+        assert f(7654321 + 1000 * mode + rep, 1 << 28, mode, ctypes.c_void_p(bad.data_ptr()),
+                 ctypes.c_void_p(ex.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0, ex.cpu().numpy()

@@ -830,3 +830,84 @@ def test_nan_operand_is_missing_data(dt):
         x = np.concatenate([nan[:1], a[:1]])
         assert oracle.nrm(x, math.inf) == a[0]
         assert oracle.nrm(x, 2.0) == oracle.nrm(a[:1].repeat(2), 2.0)
+
+
+# ---------------------------------------------------------------------------
+# the exponent-scaled hypotenuse K2 (a division-free hypot[f], Section 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_k2_exact_cases_and_symmetry(dt):
+    """K2(a, 0) = |a| exactly (sqrt(RN(a^2)) = |a|), K2(0, 0) = 0, K2 is
+    symmetric and sign-blind, inf gives inf, a NaN is missing data."""
+    r = random.Random(31)
+    info = np.finfo(dt)
+    vals = [dt(r.uniform(1, 2) * 2.0 ** r.randint(int(info.minexp) - 20, int(info.maxexp) - 1)) for _ in range(3000)]
+    vals += [info.max, info.tiny, info.smallest_subnormal, dt(1), dt(3)]
+    for v in vals:
+        assert oracle.k2(v, 0, dt) == abs(v), v
+        assert oracle.k2(0, -v, dt) == abs(v), v
+    assert oracle.k2(0, 0, dt) == 0
+    for _ in range(2000):
+        a = dt(r.uniform(-2, 2) * 2.0 ** r.randint(-30, 30))
+        b = dt(r.uniform(-2, 2) * 2.0 ** r.randint(-30, 30))
+        v = oracle.k2(a, b, dt)
+        assert v == oracle.k2(b, a, dt) == oracle.k2(-a, b, dt) == oracle.k2(a, -b, dt)
+    assert math.isinf(oracle.k2(np.inf, 1.0, dt))
+    x = np.array([np.nan, 3.0, 1e-30], dt)
+    y = np.array([3.0, np.nan, np.nan], dt)
+    assert same_bits(oracle.k2_arr(x, y), oracle.k2_arr(np.array([3.0, 3.0, 1e-30], dt), np.array([3.0, 3.0, 1e-30], dt)))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_k2_accuracy_monotone_and_scaling(dt):
+    """|K2(x, y) - hypot(x, y)| <= 1.75 eps (1 + 2^-20) hypot(x, y) against
+    mpmath when nothing underflows; K2 is non-decreasing in |x| (and |y|);
+    K2(2^j x, 2^j y) = 2^j K2(x, y) while nothing over- or underflows; the
+    largest finite pairs stay finite when the hypotenuse fits."""
+    r = random.Random(32)
+    eps = EPS_D if dt == np.float64 else EPS_S
+    worst = 0.0
+    with mpmath.workprec(300):
+        for _ in range(4000):
+            a = dt(r.uniform(1, 2) * 2.0 ** r.randint(-60, 60))
+            b = dt(r.uniform(1, 2) * 2.0 ** (math.floor(math.log2(a)) - r.choice([0, 0, 1, 2, 5, 12, 30])))
+            v = oracle.k2(a, b, dt)
+            ex = mpmath.sqrt(mpmath.mpf(float(a)) ** 2 + mpmath.mpf(float(b)) ** 2)
+            e = float(abs(mpmath.mpf(float(v)) - ex) / ex)
+            worst = max(worst, e)
+            assert e <= 1.75 * eps * (1 + 2.0 ** -20), (a, b, e / eps)
+            a2 = np.nextafter(a, dt(np.inf))
+            assert oracle.k2(a2, b, dt) >= v
+            assert oracle.k2(a, np.nextafter(b, dt(np.inf)), dt) >= v
+            j = r.randint(-20, 20)
+            assert oracle.k2(a * dt(2.0 ** j), b * dt(2.0 ** j), dt) == v * dt(2.0 ** j)
+    assert worst > 0.5 * eps
+    big = np.finfo(dt).max
+    assert math.isfinite(oracle.k2(big / dt(2), big / dt(2), dt))
+    assert math.isinf(oracle.k2(big, big, dt))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_nrm_es_against_binary128(dt):
+    """xNRMF with K2 in the whole tree: a scalar's norm is |x|; on moderately
+    varying data (n = 2^16 and 5000) the error against the binary128
+    reference is within ((1 + 1.75 eps')^depth - 1) with eps' = eps (1 +
+    2^-20), the depth of the tree (ceil(lg m) + lg P levels); c repeated n
+    times gives |c| sqrt(n) within the same bound."""
+    eps = EPS_D if dt == np.float64 else EPS_S
+    P = 64 if dt == np.float64 else 128
+    for v in (dt(3.5), dt(-1e-30), dt(7e20)):
+        assert oracle.nrm_es(np.array([v], dt)) == abs(v)
+    for n in (5000, 1 << 16):
+        x = inputs.vector(n, seed=33, vec=n % 7, dtype=dt)
+        v = oracle.nrm_es(x)
+        depth = oracle.tree_depth(n, P)
+        bound = (1 + 1.75 * eps * (1 + 2.0 ** -20)) ** depth - 1
+        e = oracle.relerr(v, x, 2.0, nthreads=4)
+        assert e <= bound, (n, e, bound)
+    c = dt(1.7)
+    n = 1 << 14
+    v = float(oracle.nrm_es(np.full(n, c, dt)))
+    bound = (1 + 1.75 * eps * (1 + 2.0 ** -20)) ** oracle.tree_depth(n, P) - 1
+    assert abs(v - 1.7 * math.sqrt(n)) <= bound * 1.7 * math.sqrt(n) + 1.7 * math.sqrt(n) * eps
