@@ -199,7 +199,7 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
             T res;
             if constexpr (FinalA) res = lane_reduce<T, OpCrHypot<T>>(r, OpCrHypot<T>{}, lane);
             else res = lane_reduce<T, Op>(r, op, lane);
-            if (lane == 0) a.out[v] = res;
+            if (lane == 0) a.out[batch ? pl.out_idx : v] = res;
         }
         if (batch) {
             unsigned long long g1 = 0;
@@ -295,25 +295,89 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     // If even the deepest work items need more ticket nodes than the
     // workspace holds, no vector is computed and all report NRM_ENOMEM.
     const bool overflow = s_nodes[blockDim.x - 1] > node_cap;
-    int64_t ib = s_items[tid] - si, nb = s_nodes[tid] - sn;
+    const int64_t total_items = s_items[blockDim.x - 1], total_nodes = s_nodes[blockDim.x - 1];
+    const int64_t nb0 = s_nodes[tid] - sn; // this thread's first ticket node (vector order)
+    const int64_t ib0 = s_items[tid] - si; // its first work item in vector order
+    // statuses and the outputs of empty or bad vectors
     for (int64_t v = v0; v < v1; ++v) {
         VecPlan pl;
         int64_t it, nd;
         int32_t st;
         plan_of(v, pl, it, nd, st);
         if (overflow && st == NRM_OK) st = NRM_ENOMEM;
-        pl.item_base = ib;
-        pl.node_base = nb;
-        plans[v] = pl;
         if (status) status[v] = st;
         if (st != NRM_OK) out[v] = T(NAN);
         else if (pl.n == 0) out[v] = T(0);
-        ib += it;
-        nb += nd;
+    }
+    // Work order: the persistent grid takes work items in index order, so
+    // the vectors are numbered longest first (a counting sort on n in
+    // quarter-octave classes, the last bucket for vectors without work
+    // items) and the
+    // plans stored in that order, their item bases increasing with the index,
+    // each with its vector's output index.  Within a bucket the order comes
+    // from one 64-bit atomic per vector that returns its slot (high 20 bits)
+    // and its first item (low 44 bits) together, so it may differ between
+    // calls: it decides which warp computes a subtree, never the tree.
+    // Ticket nodes keep the vector order.
+    // classes of a quarter octave: floor(log2 n) and the next two bits of n
+    constexpr int NB = 4 * 41 + 1;
+    __shared__ unsigned long long s_cnt[NB];
+    __shared__ int64_t s_vbase[NB], s_ibase[NB];
+    const bool sorted = B < (int64_t(1) << 20) && total_items < (int64_t(1) << 44);
+    auto bucket_of = [&](int64_t n, int64_t items) {
+        if (items == 0 || overflow) return NB - 1;
+        const int lg = 63 - __clzll((long long)n); // n >= 1
+        const int cls = lg >= 40 ? 4 * 40 + 3 : 4 * lg + (lg >= 2 ? (int)((n >> (lg - 2)) & 3) : 0);
+        return NB - 2 - cls;
+    };
+    __syncthreads(); // every reader of the scans above is done
+    for (int q = tid; q < NB; q += blockDim.x) s_cnt[q] = 0ull;
+    __syncthreads();
+    if (sorted) {
+        for (int64_t v = v0; v < v1; ++v) {
+            VecPlan pl;
+            int64_t it, nd;
+            int32_t st;
+            plan_of(v, pl, it, nd, st);
+            atomicAdd(&s_cnt[bucket_of(pl.n, it)], (1ull << 44) | (unsigned long long)(overflow ? 0 : it));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int64_t vb = 0, ibs = 0;
+        for (int q = 0; q < NB; ++q) {
+            s_vbase[q] = vb;
+            s_ibase[q] = ibs;
+            vb += (int64_t)(s_cnt[q] >> 44);
+            ibs += (int64_t)(s_cnt[q] & ((1ull << 44) - 1));
+            s_cnt[q] = 0ull;
+        }
+    }
+    __syncthreads();
+    int64_t nbr = nb0, ib_unsorted = ib0;
+    for (int64_t v = v0; v < v1; ++v) {
+        VecPlan pl;
+        int64_t it, nd;
+        int32_t st;
+        plan_of(v, pl, it, nd, st);
+        if (overflow) it = 0;
+        pl.node_base = nbr;
+        pl.out_idx = v;
+        if (sorted) {
+            const int q = bucket_of(pl.n, it);
+            const unsigned long long got = atomicAdd(&s_cnt[q], (1ull << 44) | (unsigned long long)it);
+            pl.item_base = s_ibase[q] + (int64_t)(got & ((1ull << 44) - 1));
+            plans[s_vbase[q] + (int64_t)(got >> 44)] = pl;
+        } else {
+            pl.item_base = ib_unsorted;
+            plans[v] = pl;
+            ib_unsorted += it;
+        }
+        nbr += nd;
     }
     if (tid == blockDim.x - 1) {
-        totals[0] = overflow ? 0 : s_items[tid];
-        totals[1] = s_nodes[tid];
+        totals[0] = overflow ? 0 : total_items;
+        totals[1] = total_nodes;
         *cursor = 0ull;
     }
 }
