@@ -367,8 +367,9 @@ def main():
     # A for the final reduction, and the exponent-scaled hypotenuse K2
     if rank == 0 and not args.no_batch:
         variants = {}
+        vod, vos = torch.empty_like(od), torch.empty_like(os_)
         for name, fn in (("za", nrm.nrmf_za), ("es", nrm.nrmf_es)):
-            for tag, x, o in (("d", xd, od), ("s", xs, os_)):
+            for tag, x, o in (("d", xd, vod), ("s", xs, vos)):
                 fn(x, out=o, ctx=ctx)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
