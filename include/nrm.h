@@ -367,7 +367,9 @@ void nrm_test_inject_alloc_failures(int count);
  * values) -- the integer/FP32 form the tree kernels use and the FP64-pipe
  * form -- and add the number of bitwise differences to *bad (device
  * pointer); example (device, 4 doubles) receives the first differing
- * x, y and both results. */
+ * x, y and both results.  mode 8..14: family mode - 8 with the branch-free
+ * form of checked groups, on the pairs inside its range [2^-500, 2^502)
+ * (others skipped).  NRM_EINVAL for another mode. */
 nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad, double *example,
                                 void *stream);
 

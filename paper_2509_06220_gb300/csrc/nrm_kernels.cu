@@ -51,6 +51,7 @@ template <typename T> struct TreeArgs {
     unsigned long long *cursor;    // batch: dynamic work cursor (zeroed by plan)
     unsigned *tickets;
     T *slots;
+    int levels;                    // counter-stack rows per warp: max k - G of the launch
 };
 
 // R over the P lanes held by the warp (Listing 1 with contiguous pairing):
@@ -108,11 +109,15 @@ template <class Op> struct StagesOf<Op, std::void_t<decltype(Op::kStages)>> {
     static constexpr int value = Op::kStages;
 };
 
-// dynamic shared memory of a tree block: per warp, the counter stack of MAXL
-// rows and the ring of StagesOf<Op> groups of 2^G rows (512 bytes a row)
-template <int G, class Op> constexpr size_t tree_smem_bytes(int wpb) {
-    return (size_t)wpb * ((size_t)MAXL * 512 + (size_t)StagesOf<Op>::value * (1u << G) * 512);
+// dynamic shared memory of a tree block: per warp, the counter stack of
+// `levels` rows (k - G for the deepest work item of the launch, at most
+// MAXL) and the ring of StagesOf<Op> groups of 2^G rows (512 bytes a row)
+template <int G, class Op> constexpr size_t tree_smem_bytes(int wpb, int levels) {
+    return (size_t)wpb * ((size_t)levels * 512 + (size_t)StagesOf<Op>::value * (1u << G) * 512);
 }
+
+// stack rows for work items of at most 2^kmax rows
+static int stack_levels(int kmax, int G) { return std::max(0, std::min(MAXL, kmax - G)); }
 
 template <typename T, int G, class Op, bool FinalA = false>
 __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
@@ -124,10 +129,10 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
     const bool batch = a.plans != nullptr;
     const int64_t total = batch ? *a.total_items : a.item_hi;
     extern __shared__ __align__(16) unsigned char nrm_smem[];
-    T *stk = reinterpret_cast<T *>(nrm_smem) + (threadIdx.x >> 5) * (MAXL * P);
+    T *stk = reinterpret_cast<T *>(nrm_smem) + (threadIdx.x >> 5) * (a.levels * P);
     constexpr int NS = StagesOf<Op>::value;
     typename Geo<T>::vec *ring = reinterpret_cast<typename Geo<T>::vec *>(
-        nrm_smem + (size_t)(blockDim.x >> 5) * MAXL * 512 + (size_t)(threadIdx.x >> 5) * (NS * (1u << G) * 512));
+        nrm_smem + (size_t)(blockDim.x >> 5) * a.levels * 512 + (size_t)(threadIdx.x >> 5) * (NS * (1u << G) * 512));
 
     int64_t gi;
     if (batch) {
@@ -485,7 +490,7 @@ extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
     c->sms = prop.multiProcessorCount;
     // defaults from a sweep on GB300 at n = 2^28 (the autotuner refines them)
     c->tune[NRM_F32] = nrm_tuning{3, 4, 9, 8};
-    c->tune[NRM_F64] = nrm_tuning{2, 8, 8, 16};
+    c->tune[NRM_F64] = nrm_tuning{2, 8, 9, 16};
     nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20, 1 << 16);
     if (s != NRM_OK) {
         delete c;
@@ -612,7 +617,7 @@ static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, i
     switch (tu.group_log2) {
 #define NRM_LAUNCH_G(GG)                                                                                    \
     case GG: {                                                                                              \
-        const size_t smem = tree_smem_bytes<GG, Op>(wpb);                                                  \
+        const size_t smem = tree_smem_bytes<GG, Op>(wpb, a.levels);                                        \
         cudaFuncSetAttribute(tree_kernel<T, GG, Op, FinalA>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                              (int)smem);                                                                    \
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<T, GG, Op, FinalA>, wpb * 32, smem); \
@@ -671,6 +676,7 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
     a.cursor = nullptr;
     a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>((char *)c->ws + L.slots);
+    a.levels = stack_levels(pl.k, tune_of<T>(c).group_log2);
     const int64_t warps = a.item_hi - a.item_lo;
     cudaError_t e;
     // variant 0: the combine of p; 1: Z with A (cr_hypot for the lane
@@ -861,7 +867,17 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     int64_t *totals = reinterpret_cast<int64_t *>(ws + L.totals);
     unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + L.cursor);
     const nrm_tuning &tu = tune_of<T>(c);
-    const int kmax = tu.group_log2 + MAXL;
+    // Deepest work item: vectors of offsets never overlap, so the ticket
+    // bound holds at item_log2 and a vector's k is at most item_log2 or
+    // D - DW_MAX for the longest possible vector (x_len elements); the plan
+    // kernel reports NRM_EINVAL for any vector deeper than kmax.  Segments
+    // may overlap and deepen their items, up to G + MAXL.
+    int kmax = tu.group_log2 + MAXL;
+    if (!lens) {
+        const int dmax = ceil_log2_i64(std::max<int64_t>(1, (x_len + P - 1) / P));
+        kmax = std::min(kmax, std::max(std::min(dmax, tu.item_log2), dmax - DW_MAX));
+        kmax = std::max(kmax, tu.group_log2);
+    }
     plan_kernel<T><<<1, 1024, 0, s>>>(off, lens, B, x_len, tu.item_log2, DW_MAX, kmax, nodes_bound, plans, totals,
                                       cursor, out, status);
     cudaError_t e = cudaGetLastError();
@@ -875,6 +891,7 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     a.cursor = cursor;
     a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>(ws + L.slots);
+    a.levels = stack_levels(kmax, tu.group_log2);
     const int64_t persistent = (int64_t)c->sms * 64 * tu.warps_per_block; // capped by occupancy
     e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, persistent, s); });
     return set_cuda_err(c, e, "tree_kernel launch (batch)");
@@ -957,7 +974,7 @@ nrm_status na_setup(int dev, NaDevice **out) {
         e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return NRM_ECUDA;
         int occ = 0;
-        const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB);
+        const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB, MAXL);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<double, NA_G, OpHypot<double>>,
                                                           NA_WPB * 32, smem);
         if (e != cudaSuccess) return NRM_ECUDA;
@@ -1012,7 +1029,8 @@ extern "C" nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, vo
     a.item_hi = items;
     a.tickets = tickets;
     a.slots = slots;
-    const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB);
+    a.levels = MAXL;
+    const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB, MAXL);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + NA_WPB - 1) / NA_WPB,
                                                                   (int64_t)d->sms * d->occ));
     tree_kernel<double, NA_G, OpHypot<double>><<<(unsigned)blocks, NA_WPB * 32, smem, s>>>(a, OpHypot<double>{});
@@ -1100,11 +1118,21 @@ __device__ __forceinline__ void k1d_pair(uint64_t seed, int64_t i, int mode, dou
     }
 }
 
+// mode 0..6: k1_exact on family `mode`; mode 8..14: k1_exact_fast on family
+// mode - 8, for the pairs inside its range [2^-500, 2^502) (others skipped)
 __global__ void k1d_compare_kernel(uint64_t seed, int64_t n, int mode, unsigned long long *bad, double *example) {
+    const bool fast = mode >= 8;
+    const int fam = mode & 7;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double x, y;
-        k1d_pair(seed, i, mode, x, y);
-        const double a = k1_exact(x, y), b = k1(x, y);
+        k1d_pair(seed, i, fam, x, y);
+        if (fast) {
+            const uint32_t hx = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32) & 0x7fffffffu;
+            const uint32_t hy = (uint32_t)((uint64_t)__double_as_longlong(y) >> 32) & 0x7fffffffu;
+            const uint32_t lo = (uint32_t)(1023 - 500) << 20, hi = (uint32_t)(1023 + 502) << 20;
+            if (hx < lo || hx >= hi || hy < lo || hy >= hi) continue;
+        }
+        const double a = fast ? k1_exact_fast(x, y) : k1_exact(x, y), b = k1(x, y);
         const bool same = (__double_as_longlong(a) == __double_as_longlong(b)) || (isnan(a) && isnan(b));
         if (!same) {
             if (atomicAdd(bad, 1ull) == 0ull) {
@@ -1305,7 +1333,7 @@ extern "C" nrm_status nrm_test_k2d_compare(uint64_t seed, int64_t n, int32_t mod
 
 extern "C" nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad,
                                            double *example, void *stream) {
-    if (n < 0 || !bad || !example) return NRM_EINVAL;
+    if (n < 0 || !bad || !example || mode < 0 || mode > 14 || mode == 7) return NRM_EINVAL;
     k1d_compare_kernel<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(seed, n, mode, bad, example);
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }

@@ -507,6 +507,27 @@ def test_k1_exact_matches_fp64_k1(nrm, mode):
     assert int(bad.item()) == 0, ex.cpu().numpy()
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 5, 6])
+def test_k1_fast_matches_fp64(nrm, mode):
+    """The checked-group binary64 v1_hypot (rounded 54-bit quotient, rounded
+    integer square root, one FP64 fma and one FP64 multiply) equals the FP64
+    v1_hypot of Listing 2 bit for bit on 2^30 generated pairs per family
+    inside its range [2^-500, 2^502)."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_k1d_compare
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    bad = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ex = torch.zeros(4, dtype=torch.float64, device=DEV)
+    for rep in range(4):
+        assert f(2468013 + 1000 * mode + rep, 1 << 28, 8 + mode, ctypes.c_void_p(bad.data_ptr()),
+                 ctypes.c_void_p(ex.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0, ex.cpu().numpy()
+    assert f(1, 1, 7, ctypes.c_void_p(bad.data_ptr()), ctypes.c_void_p(ex.data_ptr()), None) == nrm.NRM_EINVAL
+
+
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_autotune_keeps_bits(nrm, dt):
     """The autotuner picks a valid tuning; results before and after are
