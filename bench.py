@@ -45,8 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the ncu traffic figures in profiles/ belong to the kernel build they were
 # captured on; set to False whenever the binary64 tree kernel changes
 TRAFFIC_VALID = True
-TRAFFIC_D_2E28 = 2151.303e6 + 36.16256e6  # DNRMF: DRAM read + write of one launch at n = 2^28
-TRAFFIC_S_2E28 = 1073.889e6 + 7.24736e6  # SNRMF: the same
+TRAFFIC_D_2E28 = 2147.691776e6 + 17.6448e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1073.896192e6 + 4.558592e6  # SNRMF: the same
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -338,7 +338,7 @@ def main():
     s_bytes_gbs = BYTES_S / (s_avg * 1e-3) / 1e9
     achieved_ops = 7 * hypot_d / (d_avg * 1e-3)
     # DRAM bytes read+written per launch from an ncu capture at n = 2^28
-    # (profiles/tree_kernel_nrmf_2e28_full.md), in proportion to n otherwise
+    # (profiles/tree_kernel_nrmf_2e28_dram.md), in proportion to n otherwise
     traffic = TRAFFIC_D_2E28 * (N / float(1 << 28)) if TRAFFIC_VALID else None
     roof = {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": fp64_ops_peak / 1e9,
             "unit": "Gop/s (FP64, 7 per v1_hypot)", "frac": achieved_ops / fp64_ops_peak, "traffic": traffic,
