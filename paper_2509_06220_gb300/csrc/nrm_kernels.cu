@@ -166,8 +166,16 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
         T r[V];
         bool done = false;
         if constexpr (NS > 0) {
-            if (aligned && pl.k > G && t == (int64_t(1) << pl.k) && (start + t) * P <= pl.n)
-                done = item_tree_async<T, G, Op, NS>(xv, start, pl.k, lane, op, stk, ring, r);
+            if (pl.stride == 1 && pl.k > G && t >= (int64_t(1) << (pl.k - G)) && (start + t) * P <= pl.n) {
+                if (t == (int64_t(1) << pl.k)) {
+                    if (aligned)
+                        done = item_tree_async<T, G, Op, NS, true, 1>(xv, start, t, pl.k, lane, true, op, stk, ring, r);
+                    else
+                        done = item_tree_async<T, G, Op, NS, true, 0>(xv, start, t, pl.k, lane, false, op, stk, ring, r);
+                } else {
+                    done = item_tree_async<T, G, Op, NS, false, -1>(xv, start, t, pl.k, lane, aligned, op, stk, ring, r);
+                }
+            }
         }
         if (!done) item_tree<T, G, Op>(xv, pl.n, start, t, pl.k, lane, aligned, pl.stride, op, stk, r);
 
@@ -489,7 +497,7 @@ extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
     cudaGetDeviceProperties(&prop, device);
     c->sms = prop.multiProcessorCount;
     // defaults from a sweep on GB300 at n = 2^28 (the autotuner refines them)
-    c->tune[NRM_F32] = nrm_tuning{3, 4, 9, 8};
+    c->tune[NRM_F32] = nrm_tuning{2, 4, 9, 16};
     c->tune[NRM_F64] = nrm_tuning{2, 8, 9, 16};
     nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20, 1 << 16);
     if (s != NRM_OK) {

@@ -746,16 +746,19 @@ def test_k1f_fast_steps_exhaustive(nrm, mode):
     assert int(bad.item()) == 0, ex.cpu().numpy()
 
 
+@pytest.mark.parametrize("n", [5 * (1 << 18) + 77, 1 << 21, 3 * (1 << 19) - 5])
 @pytest.mark.parametrize("family", ["low_edge", "high_edge", "nan_pairs", "inf", "zeros", "subnormal", "mixed"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-def test_checked_group_boundaries(nrm, dt, family):
-    """The trees combine checked groups with a branch-free v1_hypot and send
-    the others to the general form; results must equal the oracle's whatever
-    values sit in a group: values straddling the ends of the checked range
-    (binary32 2^-88 and 2^118, binary64 2^-500 and 2^494), NaN pairs that
-    meet in the first combine (same lane, adjacent rows), inf, zeros and
-    subnormals, in vectors with full groups, full items and a ragged tail."""
-    n = 5 * (1 << 18) + 77
+def test_checked_group_boundaries(nrm, dt, family, n):
+    """The trees combine checked groups (full, and partial ones whose slots
+    are not all occupied) with a branch-free v1_hypot and send the others to
+    the general form; results must equal the oracle's whatever values sit
+    in a group: values straddling the ends of the checked range (binary32
+    2^-88 and 2^118, binary64 2^-500 and 2^494), NaN pairs that meet in the
+    first combine (same lane, adjacent rows), inf, zeros and subnormals.
+    Sizes: rows filling 5/8 of the slots (partial groups, ragged tail), a
+    power-of-two row count (every group and item full, the cp.async ring),
+    and 3/4 of the slots (groups of three rows, ragged tail)."""
     x = inputs.vector(n, seed=40 + len(family), vec=1, dtype=dt)
     rng = np.random.default_rng(abs(hash((family, str(dt)))) % 2 ** 31)
     P = 128 if dt == np.float32 else 64
