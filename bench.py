@@ -45,8 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the ncu traffic figures in profiles/ belong to the kernel build they were
 # captured on; set to False whenever the binary64 tree kernel changes
 TRAFFIC_VALID = True
-TRAFFIC_D_2E28 = 2147.691776e6 + 17.6448e6  # DNRMF: DRAM read + write of one launch at n = 2^28
-TRAFFIC_S_2E28 = 1073.896192e6 + 4.558592e6  # SNRMF: the same
+TRAFFIC_D_2E28 = 2150.276352e6 + 28.169984e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1074.339072e6 + 6.62912e6  # SNRMF: the same
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -258,9 +258,11 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=50000.0)
     ap.add_argument("--log2n", type=int, default=28,
                     help="vector length 2^k (28 is the benchmark; smaller only for profiling captures)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="vector length n, overriding --log2n (profiling captures of other shapes)")
     args = ap.parse_args()
     global N, BYTES_D, BYTES_S
-    N = 1 << args.log2n
+    N = args.n if args.n > 0 else 1 << args.log2n
     BYTES_D, BYTES_S = N * 8, N * 4
     if args.warmup < 3:
         args.warmup = 3
