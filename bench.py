@@ -45,8 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the ncu traffic figures in profiles/ belong to the kernel build they were
 # captured on; set to False whenever the binary64 tree kernel changes
 TRAFFIC_VALID = True
-TRAFFIC_D_2E28 = 2150.276352e6 + 28.169984e6  # DNRMF: DRAM read + write of one launch at n = 2^28
-TRAFFIC_S_2E28 = 1074.339072e6 + 6.62912e6  # SNRMF: the same
+TRAFFIC_D_2E28 = 2149.706496e6 + 27.048448e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1075.587584e6 + 8.574976e6  # SNRMF: the same
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

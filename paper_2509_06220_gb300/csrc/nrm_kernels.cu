@@ -166,14 +166,18 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
         T r[V];
         bool done = false;
         if constexpr (NS > 0) {
-            if (pl.stride == 1 && pl.k > G && t >= (int64_t(1) << (pl.k - G)) && (start + t) * P <= pl.n) {
+            if (pl.stride == 1 && pl.k > G && t >= (int64_t(1) << (pl.k - G))) {
+                const bool tail = (start + t) * P > pl.n;
                 if (t == (int64_t(1) << pl.k)) {
                     if (aligned)
-                        done = item_tree_async<T, G, Op, NS, true, 1>(xv, start, t, pl.k, lane, true, op, stk, ring, r);
+                        done = item_tree_async<T, G, Op, NS, true, 1>(xv, pl.n, start, t, pl.k, lane, true, tail, op,
+                                                                      stk, ring, r);
                     else
-                        done = item_tree_async<T, G, Op, NS, true, 0>(xv, start, t, pl.k, lane, false, op, stk, ring, r);
+                        done = item_tree_async<T, G, Op, NS, true, 0>(xv, pl.n, start, t, pl.k, lane, false, tail, op,
+                                                                      stk, ring, r);
                 } else {
-                    done = item_tree_async<T, G, Op, NS, false, -1>(xv, start, t, pl.k, lane, aligned, op, stk, ring, r);
+                    done = item_tree_async<T, G, Op, NS, false, -1>(xv, pl.n, start, t, pl.k, lane, aligned, tail, op,
+                                                                    stk, ring, r);
                 }
             }
         }
