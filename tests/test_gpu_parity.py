@@ -111,6 +111,33 @@ def test_misaligned_starts(nrm, dt):
         assert bits_equal(g, nrm.nrmf(aligned).item() if dt == np.float64 else np.float32(nrm.nrmf(aligned).item()))
 
 
+@pytest.mark.parametrize("plant", ["none", "low_edge", "inf"])
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_misaligned_long_vectors(nrm, dt, plant):
+    """Long vectors at element offsets 1-3 (not 16-byte aligned: their work
+    items fill the shared-memory ring one element at a time), with full and
+    partial items and a ragged tail, optionally with values below the
+    branch-free range or an inf planted (the item falls back to the general
+    form): bitwise equal to the oracle and to an aligned copy."""
+    rng = np.random.default_rng(7 + len(plant))
+    buf = inputs.vector((1 << 22) + 64, seed=8, vec=2, dtype=dt)
+    lo = -88 if dt == np.float32 else -500
+    for s, n in ((1, 1 << 22), (2, 3 * (1 << 20) + 17), (3, (1 << 22) - 1000)):
+        x = buf[s:s + n].copy()
+        if plant == "low_edge":
+            q = rng.choice(n, 8, replace=False)
+            x[q] = (rng.uniform(1, 2, 8) * 2.0 ** rng.integers(lo - 3, lo + 3, 8)).astype(dt)
+        elif plant == "inf":
+            x[rng.integers(0, n)] = np.inf
+        host = np.empty(n + 8, dtype=dt)
+        host[s:s + n] = x
+        xd = dev(host)[s:s + n]
+        got = nrm.nrmf(xd).cpu().numpy()
+        want = oracle.nrm(x)
+        assert bits_equal(np.asarray(got, dt), np.asarray(want, dt)), (s, n, got, want)
+        assert bits_equal(np.asarray(nrm.nrmf(dev(x)).cpu().numpy(), dt), np.asarray(want, dt))
+
+
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_sizes_primes_powers(nrm, dt):
     ns = []
