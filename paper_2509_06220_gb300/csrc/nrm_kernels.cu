@@ -101,7 +101,7 @@ __device__ __forceinline__ void load_slot(const T *src, T (&r)[Geo<T>::V]) {
 // sweep on GB300 found 64 registers best for v1_hypot in both precisions).
 // FinalA: reduce the P lane partials with the correctly rounded hypot (the
 // algorithm A; Z with A is the paper's recommended xNRMF) instead of op.
-// stages of the cp.async ring of full items (Op::kStages, default none)
+// stages of the cp.async ring of work items (Op::kStages, default none)
 template <class Op, class = void> struct StagesOf {
     static constexpr int value = 0;
 };
