@@ -260,7 +260,13 @@ def main():
                     help="vector length 2^k (28 is the benchmark; smaller only for profiling captures)")
     ap.add_argument("--n", type=int, default=0,
                     help="vector length n, overriding --log2n (profiling captures of other shapes)")
+    ap.add_argument("--p", type=float, default=2.0,
+                    help="xNRMP with this p instead of xNRMF (profiling captures of the p-norm kernels; "
+                         "the e2e, batch, serving and oracle legs and the v1_hypot roofline are left out)")
     args = ap.parse_args()
+    if args.p != 2.0:
+        args.no_e2e = args.no_cpu_baseline = args.no_batch = True
+        args.serve_seconds = 0
     global N, BYTES_D, BYTES_S
     N = args.n if args.n > 0 else 1 << args.log2n
     BYTES_D, BYTES_S = N * 8, N * 4
@@ -296,9 +302,15 @@ def main():
     xs = nrm.nrm_gen(N, seed, 0, torch.float32, device=dev)
     od = torch.empty((), dtype=torch.float64, device=dev)
     os_ = torch.empty((), dtype=torch.float32, device=dev)
+    if args.p == 2.0:
+        def step(x, o):
+            nrm.nrmf(x, out=o, ctx=ctx)
+    else:
+        def step(x, o):
+            nrm.nrmp(x, args.p, out=o, ctx=ctx)
     for _ in range(args.warmup):
-        nrm.nrmf(xd, out=od, ctx=ctx)
-        nrm.nrmf(xs, out=os_, ctx=ctx)
+        step(xd, od)
+        step(xs, os_)
     torch.cuda.synchronize()
 
     K = args.steps
@@ -308,9 +320,9 @@ def main():
         barrier()
         evs[0].record()
         for i in range(K):
-            nrm.nrmf(xd, out=od, ctx=ctx)
+            step(xd, od)
             evs[2 * i + 1].record()
-            nrm.nrmf(xs, out=os_, ctx=ctx)
+            step(xs, os_)
             evs[2 * i + 2].record()
         barrier()
     launches = ctx.launches - launches0
@@ -364,6 +376,10 @@ def main():
                       "snrmf": {"ms": s_avg, "GBps": s_bytes_gbs, "Gelem_per_s": N / (s_avg * 1e-3) / 1e9,
                                 "hbm_frac": s_bytes_gbs / hbm_peak,
                                 "traffic": TRAFFIC_S_2E28 * (N / float(1 << 28)) if TRAFFIC_VALID else None}}}
+    if args.p != 2.0:
+        # a p-norm capture: the roofline above prices v1_hypot
+        line["config"]["p"] = args.p
+        line["roofline"] = None
 
     # the other hypot variants on the same vectors (not the headline): Z with
     # A for the final reduction, and the exponent-scaled hypotenuse K2
