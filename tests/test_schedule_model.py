@@ -217,3 +217,73 @@ def test_plan_single_limits():
             assert 0 <= dw <= 20 and k <= 13 and k == D - dw
         m, D, k, dw = plan_single(1 << 28, P, 152, 8, 7, 3)
         assert (1 << dw) >= 152 * 8
+
+
+def slot_rank(s, tg, G):
+    """The kernels' row of slot s in a group of tg occupied slots: the number
+    of occupied slots before it, clamped to tg - 1 for an empty slot."""
+    r = sum(1 for q in range(s) if brev(q, G) < tg)
+    return min(r, tg - 1)
+
+
+@pytest.mark.parametrize("G", [2, 3])
+def test_ring_and_slot_rank_indices(G):
+    """The index arithmetic of the ring path for partial work items: group g
+    of an item of t rows (2^(k-G) <= t <= 2^k) has node_rows(t, g, k - G)
+    rows, copied from a running row offset; slot_rank maps each occupied
+    slot to the row the slot form assigns it (rows in slot order) and every
+    slot to a row of the group; the tail group starts where the ring's
+    groups end; and the slot form over those rows is the ceil-split tree of
+    the group's rows."""
+    U = 1 << G
+    for tg in range(1, U + 1):
+        seq, r = {}, 0
+        for s in range(U):
+            if brev(s, G) < tg:
+                seq[s] = r
+                r += 1
+        assert r == tg
+        for s in range(U):
+            assert 0 <= slot_rank(s, tg, G) < tg
+            if s in seq:
+                assert slot_rank(s, tg, G) == seq[s]
+        # the slot form (pairs of occupied slots combine, a lone one passes
+        # up) builds the ceil-split tree of the tg rows
+        def ceil_tree(lo, cnt):
+            if cnt == 1:
+                return lo
+            left = (cnt + 1) // 2
+            return (ceil_tree(lo, left), ceil_tree(lo + left, cnt - left))
+        buf = [seq.get(s) for s in range(U)]
+        occ = [s in seq for s in range(U)]
+        w = U
+        while w > 1:
+            for s in range(w // 2):
+                a, c = occ[2 * s], occ[2 * s + 1]
+                if a and c:
+                    buf[s] = (buf[2 * s], buf[2 * s + 1])
+                elif c:
+                    buf[s] = buf[2 * s + 1]
+                elif a:
+                    buf[s] = buf[2 * s]
+                occ[s] = a or c
+            w //= 2
+        assert buf[0] == ceil_tree(0, tg)
+    for k in range(G + 1, G + 7):
+        L = k - G
+        for t in range(1 << L, (1 << k) + 1):
+            pref, rows = 0, []
+            for g in range(1 << L):
+                tq = node_rows(t, g, L)
+                assert 1 <= tq <= U
+                rows.append((pref, tq))
+                pref += tq
+            assert pref == t
+            # the tail group (the last) starts at t - tg
+            last0, lastn = rows[-1]
+            assert last0 == t - lastn
+            # groups are the item's subtrees at depth L: their row starts are
+            # the root-to-node walk
+            for g, (r0, tq) in enumerate(rows):
+                assert r0 == node_start(t, g, L) and tq == node_rows(t, g, L)
+
