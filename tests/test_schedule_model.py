@@ -287,3 +287,43 @@ def test_ring_and_slot_rank_indices(G):
             for g, (r0, tq) in enumerate(rows):
                 assert r0 == node_start(t, g, L) and tq == node_rows(t, g, L)
 
+
+@pytest.mark.parametrize("P", [64, 128])
+def test_batch_stack_depth_bound(P):
+    """The batch path sizes each warp's counter stack from a bound on the
+    work-item depth k of every vector: with offsets (vectors never overlap)
+    the ticket bound 2 (x_len / P + B + 1) / 2^item_log2 + 2 holds for the
+    planner's first depth, so items never deepen, and each vector's k =
+    min(D, item_log2), raised to D - DW_MAX when the cut would be deeper than
+    DW_MAX, is at most max(min(dmax, item_log2), dmax - DW_MAX) for
+    dmax = ceil(log2(ceil(x_len / P))).  The planner's rule replayed on
+    random ragged batches, including very long vectors."""
+    DW_MAX = 20
+    rng = random.Random(P)
+    for trial in range(300):
+        item_log2 = rng.randint(4, 12)
+        B = rng.randint(1, 64)
+        kind = trial % 3
+        if kind == 0:
+            lens = [rng.randint(0, 1 << rng.randint(0, 20)) for _ in range(B)]
+        elif kind == 1:
+            lens = [1 << rng.randint(0, 36) for _ in range(B)]
+        else:
+            lens = [rng.randint(0, 1 << 40) for _ in range(B)]
+        x_len = sum(lens)
+        dmax = clog2(max(1, (x_len + P - 1) // P))
+        kmax = max(min(dmax, item_log2), dmax - DW_MAX)
+        nodes = 0
+        for n in lens:
+            if n == 0:
+                continue
+            m = (n + P - 1) // P
+            D = clog2(m)
+            k = min(D, item_log2)
+            if D - k > DW_MAX:
+                k = D - DW_MAX
+            assert k <= kmax, (n, k, kmax)
+            nodes += (1 << (D - k)) - 1
+        node_cap = (2 * (x_len // P + B + 1) >> item_log2) + 2
+        assert nodes <= node_cap, (nodes, node_cap)
+
