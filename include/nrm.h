@@ -272,10 +272,13 @@ nrm_status nrm_gen_ragged(nrm_dtype dtype, void *x, int64_t x_len, const int64_t
  *   n     : 0 <= n <= NRM_NOALLOC_MAX_N; n == 0 gives +0;
  *   out   : device pointer to one binary64, written asynchronously;
  *   stream: cudaStream_t as void* (NULL = legacy default stream).
- * Scratch: a static device array of about 1 MiB inside the library, created
- * on every device that loads the library and held until the process exits.
- * The first call on each device looks up that array's address (with the
- * device current); make that first call before any stream capture.  All
+ * Scratch: a static device array of about 2 MiB inside the library (8 KiB
+ * of ticket counters and 2 (2^11 - 1) partial-norm rows of 512 bytes),
+ * created on every device that loads the library and held until the process
+ * exits.  The first call on each device looks up that array's address (with
+ * the device current); make that first call before any stream capture.  A
+ * cudaDeviceReset destroys the array with the device's context: do not call
+ * this entry point after one in the same process.  All
  * calls on a device share the array and it keeps the last call's contents:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * give wrong results -- order them on one stream.
@@ -435,6 +438,26 @@ nrm_status nrm_test_k2d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned
 /* Test hook: copy the first `count` ticket counters of the context's
  * workspace to host memory (synchronous).  Between calls they are all zero. */
 nrm_status nrm_test_read_tickets(const nrm_ctx *ctx, uint32_t *host, int64_t count);
+
+/*
+ * Measurement hook (the paper has no counterpart): a register-only
+ * throughput probe of one SM pipe, with which the benchmark measures the
+ * ceiling it holds the tree kernels to instead of assuming a nominal rate.
+ *   kind          : 0 = binary64 fma (DFMA), 1 = binary64 multiply (DMUL),
+ *                   2 = binary32 fma (FFMA);
+ *   iters         : >= 1; every thread runs 8 independent dependency chains
+ *                   of 4 iters operations each;
+ *   blocks_per_sm : 1..8 blocks of 256 threads per SM of the current device;
+ *   sink          : device pointer to one double, never written in practice
+ *                   (it keeps the chains alive through the optimiser);
+ *   thread_ops    : host pointer (may be NULL) that receives the number of
+ *                   operations the launch performs.
+ * Asynchronous on `stream`; time it with CUDA events on that stream.
+ * Errors: NRM_EINVAL for a bad kind, iters < 1, blocks_per_sm outside 1..8
+ * or sink == NULL; NRM_EDEVICE without a current device.
+ */
+nrm_status nrm_probe_pipe(int32_t kind, int64_t iters, int32_t blocks_per_sm, double *sink, int64_t *thread_ops,
+                          void *stream);
 
 #ifdef __cplusplus
 }

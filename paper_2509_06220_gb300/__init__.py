@@ -118,6 +118,7 @@ def load():
         "nrm_srv_destroy": (st, [vp]),
         "nrm_test_inject_alloc_failures": (None, [ctypes.c_int]),
         "nrm_test_read_tickets": (st, [vp, vp, i64]),
+        "nrm_probe_pipe": (st, [i32, i64, i32, vp, ctypes.POINTER(i64), vp]),
     }
     for name, (res, args) in sigs.items():
         if hasattr(L, name):
@@ -560,6 +561,39 @@ def nrm_matrix(buf, M, N, lda, p=2.0, out=None, stream=None, ctx=None):
                           ctypes.c_void_p(out.data_ptr()), _stream(stream))
     c.check(r, "nrm_matrix")
     return out
+
+
+PIPE_DFMA, PIPE_DMUL, PIPE_FFMA = 0, 1, 2
+
+
+def probe_pipe(kind=PIPE_DFMA, iters=4096, blocks_per_sm=8, reps=3, device=None):
+    """Measured throughput of one SM pipe (nrm_probe_pipe): operations per
+    second over all SMs, the best of `reps` launches timed with CUDA events
+    on the current stream after one warm-up launch."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    ops = ctypes.c_int64()
+    L = load()
+
+    def launch():
+        r = L.nrm_probe_pipe(int(kind), int(iters), int(blocks_per_sm), ctypes.c_void_p(sink.data_ptr()),
+                             ctypes.byref(ops), _stream(None))
+        if r != NRM_OK:
+            raise NrmError(r, "nrm_probe_pipe")
+
+    launch()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        launch()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return ops.value / (best * 1e-3)
 
 
 def nrmf_complex(z, out=None, stream=None, ctx=None):

@@ -948,15 +948,22 @@ extern "C" nrm_status nrm_batch(nrm_ctx *ctx, nrm_dtype dtype, const void *x, in
 // created when the library is loaded onto a device and held until the
 // process exits.  It is shared by every call on that device and keeps the
 // last call's contents; the tickets are cleared on the stream at the start of
-// each call.
+// each call.  The array's device address is looked up once per device; a
+// cudaDeviceReset destroys the array with the context, after which this
+// entry point must not be called again in the process.
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int NA_DW_MAX = 10;                                // at most 2^10 work items
+// Size limit: n <= 2^29 gives m <= 2^23 rows, a row tree of depth D <= 23,
+// and with at most 2^11 work items each item holds k = D - dw <= 12 =
+// NA_G + MAXL levels, the deepest the counter stack supports.
+constexpr int NA_DW_MAX = 11;                                // at most 2^11 work items
 constexpr int64_t NA_NODES = (int64_t(1) << NA_DW_MAX) - 1;  // internal tree nodes
-constexpr size_t NA_TICKET_BYTES = 4096;                     // >= NA_NODES * 4, slot-aligned
+constexpr size_t NA_TICKET_BYTES = 8192;                     // >= NA_NODES * 4, slot-aligned
 constexpr size_t NA_SLOT_BYTES = (size_t)2 * NA_NODES * 512; // one 512-byte row per child node
 constexpr int NA_G = 2, NA_WPB = 4;
+static_assert(NA_TICKET_BYTES >= (size_t)NA_NODES * 4 && NA_TICKET_BYTES % 512 == 0, "ticket area");
+static_assert(NA_DW_MAX + NA_G + MAXL >= 23, "n = 2^29 (2^23 rows) must fit the scratch and the stack");
 constexpr int NA_MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char nrm_noalloc_scratch[NA_TICKET_BYTES + NA_SLOT_BYTES];

@@ -5,8 +5,9 @@ whole device, and some applications forbid allocations outside their own
 allocator or budget); this entry point keeps its scratch in a static device
 array inside the library instead.  These tests call it through the C ABI and
 check it against nrmf_d, bit for bit, on two calls in a row (the second
-call reuses the scratch the first left behind), plus its size limit and the
-empty vector.  The file is collected last so that a failure here stops a
+call reuses the scratch the first left behind), at sizes up to its
+documented maximum of 2^29 elements, plus its size limit and the empty
+vector.  The file is collected last so that a failure here stops a
 -x run only after every other test has run.
 """
 import ctypes
@@ -57,12 +58,30 @@ def test_noalloc_matches_nrmf_d_two_calls_in_a_row(lib):
     assert np.float64(again.item()).tobytes() == w[0].tobytes()
 
 
+@pytest.mark.parametrize("n", [(1 << 28) + 1, (1 << 29) - 777, 1 << 29])
+def test_noalloc_up_to_its_documented_maximum(lib, n):
+    """Every n up to NRM_NOALLOC_MAX_N = 2^29 is accepted and bitwise equal
+    to nrmf_d: the deepest trees (2^23 rows) use all 2^11 work items and the
+    full counter stack."""
+    nrm, L = lib
+    dev = "cuda:0"
+    x = nrm.nrm_gen(n, 23, 0, torch.float64, device=dev)
+    want = torch.empty((), dtype=torch.float64, device=dev)
+    nrm.nrmf(x, out=want)
+    got = torch.full((), float("nan"), dtype=torch.float64, device=dev)
+    assert L.nrmf_d_noalloc(ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(got.data_ptr()), _stream()) == 0
+    torch.cuda.synchronize()
+    assert np.float64(got.item()).tobytes() == np.float64(want.item()).tobytes(), (got.item(), want.item())
+    del x
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_limits(lib):
     nrm, L = lib
     x = torch.ones(4, dtype=torch.float64, device="cuda:0")
     out = torch.full((), 7.0, dtype=torch.float64, device="cuda:0")
     s = _stream()
-    too_big = (1 << 29) + 1
+    too_big = (1 << 29) + 1  # NRM_NOALLOC_MAX_N + 1
     assert L.nrmf_d_noalloc(ctypes.c_void_p(x.data_ptr()), too_big, ctypes.c_void_p(out.data_ptr()), s) == \
         nrm.NRM_EINVAL
     assert L.nrmf_d_noalloc(ctypes.c_void_p(x.data_ptr()), -1, ctypes.c_void_p(out.data_ptr()), s) == nrm.NRM_EINVAL
