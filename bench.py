@@ -12,13 +12,25 @@ Printed as one JSON line (rank 0):
   e2e        the same metric through the C ABI's host-buffer entry point
              (nrm_host: pinned host input, chunked H2D copies overlapped with
              the tree, result read back), copies inside the timed region;
-  roofline   for the dominant kernel (the binary64 tree kernel): its
-             algorithmic work per launch over its CUDA-event launch time,
-             against the measured or unit-count peak (see DESIGN.md);
-  cpu_baseline  the C oracle on the same step, single-threaded;
-  parts      per-precision figures and the ragged-batch workload (4096
-             vectors, log-uniform lengths in [1, 2^18]) as graph replays
-             versus one launch per vector.
+  roofline   for the dominant kernel (the binary64 tree kernel): the slowest
+             of three floors -- its bytes at the measured HBM copy rate, its
+             FP64 instructions (one DFMA and one DMUL per v1_hypot) at the
+             FP64 rate measured here by a register-only probe, and its
+             thread-instructions (ncu count per element) at the issue rate
+             of 4 warp-instructions per SM per clock -- against its
+             CUDA-event launch time;
+  cpu_baseline  the C oracle on the same step, on all host cores (its thread
+             driver) and on one;
+  parts      per-precision figures, the hypot variants, config 0 (one FP64
+             vector of 2^20: median launch and end-to-end latency), config 2
+             (4096 ragged vectors, lengths log-uniform in [1, 2^18]: graph
+             replay of the persistent launch against one launch per vector,
+             both captured in CUDA graphs), config 3 (1024 vectors of 2^16,
+             p in {1, 1.5, 3, 7.5}, one batch per p and one with a p per
+             vector) and config 4 (the serving trace: Poisson arrivals at
+             50k/s for 60 s through the continuous-batching server, the
+             one-request-per-launch form on a prefix, the closed-loop
+             capacity and a run below it).
 Multi-GPU (torchrun): every rank computes its own pair of vectors (seed
 1 + rank); there is no data-path collective ("weak" scaling).
 --impl reference times the oracle (the reference arm for this build) on a
@@ -42,11 +54,15 @@ METRIC = "DNRMF+SNRMF GB/s at n=2^28 (FP64 2 GiB + FP32 1 GiB per step)"
 WORKLOAD = ("xNRMF of one FP64 and one FP32 vector of n=2^28 each, x_i = s*m*2^e, s=+-1, m uniform in [1,2), "
             "e uniform in [-20,20], seed 1 (+rank)")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# the ncu traffic figures in profiles/ belong to the kernel build they were
-# captured on; set to False whenever the binary64 tree kernel changes
-TRAFFIC_VALID = True
+# Figures from ncu captures of the kernel build they were taken on (their
+# summaries are committed beside the code); set the flag to False whenever
+# the binary64 tree kernel changes, and re-capture.
+NCU_VALID = True
 TRAFFIC_D_2E28 = 2149.706496e6 + 27.048448e6  # DNRMF: DRAM read + write of one launch at n = 2^28
 TRAFFIC_S_2E28 = 1075.587584e6 + 8.574976e6  # SNRMF: the same
+INST_PER_ELEM_D = 179.5  # DNRMF: smsp__inst_executed.sum x 32 / n at n = 2^26 (thread-instructions per element)
+FP64_PER_COMBINE_D = 2   # DNRMF: one DFMA (S = 1 + Q^2) and one DMUL (h = M s) per v1_hypot
+ISSUE_PER_SM_CLK = 4 * 32  # thread-instructions an SM issues per clock (4 schedulers x 1 warp-instruction)
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -134,9 +150,10 @@ def aggregate(total_ms, world, steps, bytes_per_step, pg=None, device=None):
 
 
 def run_reference(args):
-    """The oracle (plain serial C) on a bounded sample of the workload:
-    each step computes xNRMF of the first 2^25 elements of the FP64 and of
-    the FP32 vector (the same generator), single-threaded."""
+    """The oracle (plain serial C) on a bounded sample of the workload, on
+    all host cores: each step computes xNRMF of the first 2^26 elements of
+    the FP64 and of the FP32 vector (the same generator) with the oracle's
+    thread driver (the top splits of the same tree on separate threads)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -144,31 +161,136 @@ def run_reference(args):
 
     import oracle
     from paper_2509_06220_gb300 import inputs
-    ns = 1 << 25
+    ns = 1 << 26
+    nproc = os.cpu_count() or 1
+    threads = 1 << max(0, (nproc - 1).bit_length()) if nproc > 1 else 1
     xd = inputs.vector(ns, seed=1, vec=0, dtype=np.float64)
     xs = inputs.vector(ns, seed=1, vec=0, dtype=np.float32)
     for _ in range(args.warmup):
-        oracle.nrm(xd)
-        oracle.nrm(xs)
+        oracle.nrm_par(xd, threads=threads)
+        oracle.nrm_par(xs, threads=threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.nrm(xd)
-        oracle.nrm(xs)
+        oracle.nrm_par(xd, threads=threads)
+        oracle.nrm_par(xs, threads=threads)
     dt = time.perf_counter() - t0
     gbs = args.steps * ns * 12 / dt / 1e9
-    sample = "first 2^25 elements of each vector per step (FP64 + FP32), oracle single-threaded"
+    sample = ("first 2^26 elements of each vector per step (FP64 + FP32), oracle thread driver on %d threads "
+              "(%d host cores, %s)" % (threads, nproc, cpu_model()))
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "sample_n": ns},
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.split(":")[0].strip() in ("Model name", "Model"):
+                v = l.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith(("model name", "cpu part")):
+                return l.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def event_ms(torch, fn, reps):
+    """Average device time of fn() over reps calls, CUDA events on the
+    current stream, after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def roofline_d(ms, n, fp64_rate, fp64_src, hbm_gbs, hbm_src, sms, sm_mhz):
+    """The roofline of one DNRMF launch of n elements taking ms: the slowest
+    of its floors (HBM bytes, FP64 instructions, issued instructions); the
+    fraction is that floor's time over the launch time."""
+    floors = {"hbm": n * 8 / (hbm_gbs * 1e9) * 1e3,
+              "fp64_pipe": FP64_PER_COMBINE_D * (n - 1) / fp64_rate * 1e3,
+              "issue": INST_PER_ELEM_D * n / (sms * ISSUE_PER_SM_CLK * sm_mhz * 1e6) * 1e3}
+    if not NCU_VALID:
+        floors.pop("issue")
+    bind = max(floors, key=floors.get)
+    if bind == "hbm":
+        r = {"bound": "hbm", "achieved": n * 8 / (ms * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+             "peak_source": hbm_src}
+    elif bind == "fp64_pipe":
+        r = {"bound": "alu", "achieved": FP64_PER_COMBINE_D * (n - 1) / (ms * 1e-3) / 1e9, "peak": fp64_rate / 1e9,
+             "unit": "G FP64 instructions/s (DFMA + DMUL, one each per v1_hypot)", "peak_source": fp64_src}
+    else:
+        r = {"bound": "alu", "achieved": INST_PER_ELEM_D * n / (ms * 1e-3) / 1e9,
+             "peak": sms * ISSUE_PER_SM_CLK * sm_mhz / 1e3,
+             "unit": "G thread-instructions/s issued (%.1f per element, ncu)" % INST_PER_ELEM_D,
+             "peak_source": "%d SMs x 4 warp-instructions per clock x %.0f MHz (the maximum SM clock)" % (sms, sm_mhz)}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["binding_floor"] = bind
+    r["floors_ms"] = floors
+    r["launch_ms"] = ms
+    return r
+
+
+def time_config0(nrm, torch, ctx, dev):
+    """Config 0: DNRMF on one FP64 vector of 2^20 (seed 0): the median of 200
+    launches timed one by one with CUDA events, and the median end-to-end
+    latency of 100 calls through the host-buffer entry point (pinned input,
+    result on the host), both bitwise against the oracle."""
+    import numpy as np
+
+    import oracle
+    n = 1 << 20
+    x = nrm.nrm_gen(n, 0, 0, torch.float64, device=dev)
+    out = torch.empty((), dtype=torch.float64, device=dev)
+    for _ in range(5):
+        nrm.nrmf(x, out=out, ctx=ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record()
+        nrm.nrmf(x, out=out, ctx=ctx)
+        b.record()
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    hx = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hx.copy_(x)
+    lat = []
+    for i in range(105):
+        t0 = time.perf_counter()
+        v = nrm.nrm_host(hx, ctx=ctx, device=dev.index or 0)
+        if i >= 5:
+            lat.append((time.perf_counter() - t0) * 1e3)
+    lat.sort()
+    want = oracle.nrm(hx.numpy())
+    return {"n": n, "launches": len(ms), "median_ms": ms[len(ms) // 2], "p10_ms": ms[len(ms) // 10],
+            "p90_ms": ms[9 * len(ms) // 10], "GBps_median": n * 8 / (ms[len(ms) // 2] * 1e-3) / 1e9,
+            "e2e_calls": len(lat), "e2e_median_ms": lat[len(lat) // 2], "e2e_p90_ms": lat[9 * len(lat) // 10],
+            "bitwise_equal_oracle": bool(np.float64(out.item()).tobytes() == want.tobytes()
+                                         and np.float64(v).tobytes() == want.tobytes())}
+
+
 def time_batch(nrm, torch, ctx, dev):
-    """Ragged batch of 4096 FP64 vectors, lengths log-uniform in [1, 2^18]:
-    graph replay of the persistent launch versus one launch per vector."""
+    """Config 2: a ragged batch of 4096 vectors, lengths log-uniform in
+    [1, 2^18], FP64 and FP32: replays of the captured persistent launch
+    against the 4096 single-vector launches captured into one CUDA graph
+    (so neither side pays host launch overhead), bitwise equal."""
     import numpy as np
 
     from paper_2509_06220_gb300 import inputs
@@ -185,62 +307,155 @@ def time_batch(nrm, torch, ctx, dev):
         bctx = nrm.Context(0)
         tuned = bctx.autotune(nrm.NRM_F64 if td == torch.float64 else nrm.NRM_F32, L)
         g = nrm.nrm_batch_graph(x, offd, ctx=bctx)
-        for _ in range(3):
-            g.launch()
-        torch.cuda.synchronize()
-        reps = 20
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            g.launch()
-        e1.record()
-        torch.cuda.synchronize()
-        t_graph = e0.elapsed_time(e1) / reps
+        t_graph = event_ms(torch, g.launch, 20)
         single = torch.empty(4096, dtype=td, device=dev)
         views = [x[off[i]:off[i + 1]] for i in range(4096)]
-        for i in range(4096):
-            nrm.nrmf(views[i], out=single[i], ctx=ctx)
+
+        def singles():
+            for i in range(4096):
+                nrm.nrmf(views[i], out=single[i], ctx=ctx)
+
+        singles()  # sizes the workspace before the capture
         torch.cuda.synchronize()
-        e0.record()
-        for i in range(4096):
-            nrm.nrmf(views[i], out=single[i], ctx=ctx)
-        e1.record()
+        t0 = time.perf_counter()
+        singles()
         torch.cuda.synchronize()
-        t_single = e0.elapsed_time(e1)
+        t_loop = (time.perf_counter() - t0) * 1e3
+        cg = torch.cuda.CUDAGraph()
+        form = "4096 nrmf_* launches captured in one CUDA graph"
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(cg, stream=s, capture_error_mode="thread_local"):
+                    singles()
+            torch.cuda.synchronize()
+            t_single = event_ms(torch, cg.replay, 3)
+        except RuntimeError as e:  # capture refused: time the launches from the host loop instead
+            form = "4096 nrmf_* launches from a host loop (graph capture failed: %s)" % str(e)[:120]
+            t_single = t_loop
         same = bool(torch.equal(single.view(torch.int64 if td == torch.float64 else torch.int32),
                                 g.out.view(torch.int64 if td == torch.float64 else torch.int32)))
         out["batch_" + name] = {"norms_per_s": 4096 / (t_graph * 1e-3), "ms_per_batch": t_graph,
                                 "elements": int(off[-1]), "GBps": off[-1] * x.element_size() / (t_graph * 1e-3) / 1e9,
                                 "one_launch_per_vector_ms": t_single,
                                 "one_launch_per_vector_norms_per_s": 4096 / (t_single * 1e-3),
-                                "bitwise_equal_to_single": same, "tuning": tuned}
+                                "one_launch_per_vector_form": form,
+                                "host_loop_ms": t_loop, "bitwise_equal_to_single": same, "tuning": tuned}
+        del cg
         g.close()
         bctx.close()
         del x
     return out
 
 
-def time_serving(nrm, seconds, rate):
-    """Serving (config 4): Poisson arrivals at `rate`/s for `seconds`,
-    lengths log-uniform in [2^4, 2^24], FP32/FP64 1:1, p = 2 (80 %) else
-    1.5 or 3; inputs generated on the device at admission; 8 GiB budget.
-    The same trace through the continuous-batching server and through the
-    one-request-per-launch form."""
+def time_config3(nrm, torch, dev):
+    """Config 3: batched xNRMP, 1024 vectors of 2^16 elements (e in [-8, 8]),
+    FP64 and FP32, one captured batch per p in {1, 1.5, 3, 7.5} and one batch
+    with the four p assigned per vector in turn (the p_dev form)."""
     import numpy as np
-    tr = nrm.serving_trace(rate, seconds, seed=0)
-    res, norms = {}, {}
-    for name, (ns, mb) in (("batched", (4, 256)), ("one_request_per_launch", (1, 1))):
-        srv = nrm.Server(budget_bytes=8 << 30, nstreams=ns, max_batch=mb)
+    B, n = 1024, 1 << 16
+    off = torch.arange(0, (B + 1) * n, n, dtype=torch.int64, device=dev)
+    res = {}
+    for name, td in (("f64", torch.float64), ("f32", torch.float32)):
+        x = nrm.nrm_gen_ragged(off, seed=3, dtype=td, emin=-8, emax=8)
+        r = {}
+        outs = {}
+        for p in (1.0, 1.5, 3.0, 7.5):
+            g = nrm.nrm_batch_graph(x, off, p)
+            ms = event_ms(torch, g.launch, 10)
+            outs[p] = g.out.clone()
+            g.close()
+            r["p=%g" % p] = {"ms": ms, "norms_per_s": B / (ms * 1e-3), "Gelem_per_s": B * n / (ms * 1e-3) / 1e9}
+        pv = torch.tensor(np.tile([1.0, 1.5, 3.0, 7.5], B // 4), dtype=torch.float64, device=dev)
+        g = nrm.nrm_batch_graph(x, off, pv)
+        ms = event_ms(torch, g.launch, 10)
+        mixed = g.out.clone()
+        g.close()
+        same = all(torch.equal(mixed[i::4], outs[p][i::4]) for i, p in enumerate((1.0, 1.5, 3.0, 7.5)))
+        r["p_per_vector"] = {"ms": ms, "norms_per_s": B / (ms * 1e-3), "Gelem_per_s": B * n / (ms * 1e-3) / 1e9,
+                             "bitwise_equal_to_one_p_batches": bool(same)}
+        res[name] = r
+        del x
+    return res
+
+
+def _replay(nrm, tr, nstreams, max_batch):
+    srv = nrm.Server(budget_bytes=8 << 30, nstreams=nstreams, max_batch=max_batch)
+    try:
         v, lat, rep = srv.replay(tr)
+    finally:
         srv.close()
-        norms[name] = v
-        res[name] = {k: rep[k] for k in ("completed", "rejected", "max_queue", "steps", "launches", "p50_ms",
-                                           "p99_ms", "mean_ms", "max_ms", "wall_s", "norms_per_s", "elements_per_s",
-                                           "peak_bytes", "arena_bytes")}
-    L = np.array([tr[i].n for i in range(len(tr))])
+    return v, lat, rep
+
+
+REPORT_KEYS = ("completed", "rejected", "max_queue", "steps", "launches", "p50_ms", "p99_ms", "mean_ms", "max_ms",
+               "wall_s", "norms_per_s", "elements_per_s", "peak_bytes", "arena_bytes")
+
+
+def _serve_summary(nrm, tr, lat, rep, window_s=10.0):
+    import numpy as np
+    rec = nrm.trace_records(tr)
+    arr = rec["arrival_s"]
+    out = {k: rep[k] for k in REPORT_KEYS}
+    steps = max(rep["steps"], 1)
+    out["host_launch_ms_per_step"] = rep["host_launch_s"] * 1e3 / steps
+    out["host_retire_ms_per_step"] = rep["host_retire_s"] * 1e3 / steps
+    out["host_us_per_request"] = (rep["host_launch_s"] + rep["host_retire_s"]) * 1e6 / max(rep["completed"], 1)
+    out["gpu_ms_per_step"] = rep["gpu_step_s"] * 1e3 / steps
+    out["requests_per_step"] = rep["completed"] / steps
+    out["launches_per_step"] = rep["launches"] / steps
+    T = float(arr[-1]) if arr.size else 0.0
+    if T >= 2 * window_s:
+        first = lat[arr < window_s]
+        last = lat[arr >= T - window_s]
+        p_first, p_last = float(np.percentile(first, 99)), float(np.percentile(last, 99))
+        out["p99_first_%gs_ms" % window_s] = p_first
+        out["p99_last_%gs_ms" % window_s] = p_last
+        out["p99_bounded"] = bool(p_last <= 1.5 * p_first)
+    return out
+
+
+def time_serving(nrm, seconds, rate, baseline_seconds, saturation):
+    """Config 4: Poisson arrivals at `rate`/s for `seconds`, lengths
+    log-uniform in [2^4, 2^24], FP32/FP64 1:1, p = 2 (80 %) else 1.5 or 3;
+    inputs generated on the device at admission; 8 GiB budget.  The trace
+    through the continuous-batching server; the one-request-per-launch form
+    on its first `baseline_seconds`; then the closed-loop capacity (a
+    backlog of the trace's first 3 s, all arriving at once) and a 20 s run
+    at 90 % of that capacity.  p99 is "bounded" when the p99 of the last
+    10 s of arrivals is at most 1.5x that of the first 10 s."""
+    import numpy as np
+    res = {}
+    tr = nrm.serving_trace(rate, seconds, seed=0)
+    rec = nrm.trace_records(tr)
+    v, lat, rep = _replay(nrm, tr, 4, 256)
+    res["batched"] = _serve_summary(nrm, tr, lat, rep)
+    nb = int(np.searchsorted(rec["arrival_s"], baseline_seconds))
+    if nb > 0:
+        pre = (nrm.Request * nb).from_buffer_copy(rec[:nb].tobytes())
+        vb, latb, repb = _replay(nrm, pre, 1, 1)
+        res["one_request_per_launch"] = _serve_summary(nrm, pre, latb, repb)
+        res["one_request_per_launch"]["trace_prefix_s"] = baseline_seconds
+        # the batched server on the same prefix alone, for the like-for-like p99
+        vp, latp, repp = _replay(nrm, pre, 4, 256)
+        res["batched_on_prefix"] = _serve_summary(nrm, pre, latp, repp)
+        res["bitwise_equal"] = bool(vb.tobytes() == v[:nb].tobytes() == vp.tobytes())
+    if saturation:
+        nbk = int(np.searchsorted(rec["arrival_s"], min(3.0, seconds)))
+        back = rec[:nbk].copy()
+        back["arrival_s"] = 0.0
+        bt = (nrm.Request * nbk).from_buffer_copy(back.tobytes())
+        _, _, repc = _replay(nrm, bt, 4, 256)
+        cap = repc["completed"] / max(repc["wall_s"], 1e-9)
+        sat = {"closed_loop_norms_per_s": cap, "backlog_requests": nbk}
+        r2 = 0.9 * cap
+        tr2 = nrm.serving_trace(r2, 20.0, seed=1)
+        _, lat2, rep2 = _replay(nrm, tr2, 4, 256)
+        sat["run_at_90pct"] = dict(_serve_summary(nrm, tr2, lat2, rep2), rate_per_s=r2, seconds=20.0)
+        res["saturation"] = sat
+    L = rec["n"]
     res["trace"] = {"rate_per_s": rate, "seconds": seconds, "requests": len(tr), "mean_length": float(L.mean()),
                     "offered_elements_per_s": float(L.sum() / seconds)}
-    res["bitwise_equal"] = bool(norms["batched"].tobytes() == norms["one_request_per_launch"].tobytes())
     return res
 
 
@@ -252,10 +467,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=1.0,
+    ap.add_argument("--no-batch", action="store_true", help="skip configs 0, 2 and 3 and the hypot variants")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the serving trace (config 4 runs 60 s; 0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=50000.0)
+    ap.add_argument("--serve-baseline-seconds", type=float, default=0.5,
+                    help="prefix of the trace served one request per launch")
+    ap.add_argument("--no-saturation", action="store_true")
     ap.add_argument("--log2n", type=int, default=28,
                     help="vector length 2^k (28 is the benchmark; smaller only for profiling captures)")
     ap.add_argument("--n", type=int, default=0,
@@ -297,6 +515,9 @@ def main():
         torch.cuda.synchronize()
 
     ctx = nrm.context(local)
+    # the FP64 pipe's measured rate (register-only DFMA chains), before the
+    # timed region
+    fp64_rate = nrm.probe_pipe(nrm.PIPE_DFMA, iters=4096, blocks_per_sm=8)
     seed = 1 + rank
     xd = nrm.nrm_gen(N, seed, 0, torch.float64, device=dev)
     xs = nrm.nrm_gen(N, seed, 0, torch.float32, device=dev)
@@ -337,32 +558,23 @@ def main():
 
     peaks = load_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_src = "measured hbm_gbs (copy)" if hbm_peak else "fallback 6800 GB/s"
     hbm_peak = hbm_peak or 6800.0
     sm_max = peaks.get("sm_max_mhz") or 2070.0
-    # Compute roofline of the dominant kernel (binary64 tree): 7 IEEE
-    # operations per v1_hypot (Listing 2's one-statement-one-instruction
-    # count) against GB300's FP64 rate from unit counts and clocks: SMs x 2
-    # FP64 FMA per clock x the maximum SM clock (1.25 TFLOP/s).  The HBM view
-    # of the same kernel is reported in parts.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp64_ops_peak = sms * 2 * sm_max * 1e6
-    hypot_d = N - 1
     d_bytes_gbs = BYTES_D / (d_avg * 1e-3) / 1e9
     s_bytes_gbs = BYTES_S / (s_avg * 1e-3) / 1e9
-    achieved_ops = 7 * hypot_d / (d_avg * 1e-3)
-    # DRAM bytes read+written per launch from an ncu capture at n = 2^28
-    # (profiles/tree_kernel_nrmf_2e28_dram.md), in proportion to n otherwise
-    traffic = TRAFFIC_D_2E28 * (N / float(1 << 28)) if TRAFFIC_VALID else None
-    roof = {"bound": "alu", "achieved": achieved_ops / 1e9, "peak": fp64_ops_peak / 1e9,
-            "unit": "Gop/s (FP64, 7 per v1_hypot)", "frac": achieved_ops / fp64_ops_peak, "traffic": traffic,
-            "kernel": "tree_kernel<double,%d,OpHypot>" % ctx.tuning_for(nrm.NRM_F64).group_log2,
-            "peak_source": "unit counts x clock (%d SMs x 2 x %.0f MHz)" % (sms, sm_max), "launch_ms": d_avg,
-            "hbm_view": {"achieved": d_bytes_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": d_bytes_gbs / hbm_peak,
-                         "peak_source": peak_src + " hbm_gbs"},
-            "note": "frac > 1 is possible: the roofline prices v1_hypot at 7 FP64 operations (one of them a "
-                    "division, one a square root); this kernel computes the same correctly rounded results with "
-                    "integer/FP32 instructions plus one DFMA and one DMUL (bitwise parity with the oracle)"}
+    roof = roofline_d(d_avg, N, fp64_rate, "measured here: nrm_probe_pipe DFMA chains, %d SMs x 8 blocks" % sms,
+                      hbm_peak, hbm_src, sms, sm_max)
+    # DRAM bytes read+written per launch from an ncu capture at n = 2^28, in
+    # proportion to n otherwise
+    roof["traffic"] = TRAFFIC_D_2E28 * (N / float(1 << 28)) if NCU_VALID else None
+    roof["kernel"] = "tree_kernel<double,%d,OpHypot>" % ctx.tuning_for(nrm.NRM_F64).group_log2
+    roof["hbm_view"] = {"achieved": d_bytes_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": d_bytes_gbs / hbm_peak}
+    roof["note"] = ("algorithmic view of Listing 2: 7 IEEE operations per v1_hypot = %.1f Gop/s; this kernel "
+                    "computes the same correctly rounded results with integer/FP32 instructions plus one DFMA and "
+                    "one DMUL, so the floors above price the instructions it executes" %
+                    (7 * (N - 1) / (d_avg * 1e-3) / 1e9))
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32", "data": "synthetic",
@@ -371,11 +583,11 @@ def main():
                        else "single GPU"},
             "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
             "parts": {"dnrmf": {"ms": d_avg, "GBps": d_bytes_gbs, "Gelem_per_s": N / (d_avg * 1e-3) / 1e9,
-                                "Ghypot_per_s": hypot_d / (d_avg * 1e-3) / 1e9,
-                                "fp64_pipe_peak_Gops": fp64_ops_peak / 1e9},
+                                "Ghypot_per_s": (N - 1) / (d_avg * 1e-3) / 1e9},
                       "snrmf": {"ms": s_avg, "GBps": s_bytes_gbs, "Gelem_per_s": N / (s_avg * 1e-3) / 1e9,
                                 "hbm_frac": s_bytes_gbs / hbm_peak,
-                                "traffic": TRAFFIC_S_2E28 * (N / float(1 << 28)) if TRAFFIC_VALID else None}}}
+                                "traffic": TRAFFIC_S_2E28 * (N / float(1 << 28)) if NCU_VALID else None},
+                      "fp64_probe_Gops": fp64_rate / 1e9}}
     if args.p != 2.0:
         # a p-norm capture: the roofline above prices v1_hypot
         line["config"]["p"] = args.p
@@ -388,15 +600,7 @@ def main():
         vod, vos = torch.empty_like(od), torch.empty_like(os_)
         for name, fn in (("za", nrm.nrmf_za), ("es", nrm.nrmf_es)):
             for tag, x, o in (("d", xd, vod), ("s", xs, vos)):
-                fn(x, out=o, ctx=ctx)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record()
-                for _ in range(5):
-                    fn(x, out=o, ctx=ctx)
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / 5
+                ms = event_ms(torch, lambda: fn(x, out=o, ctx=ctx), 5)
                 variants["%snrmf_%s" % (tag, name)] = {"ms": ms, "GBps": N * x.element_size() / (ms * 1e-3) / 1e9}
         line["parts"]["variants"] = variants
 
@@ -427,25 +631,38 @@ def main():
         del hd, hs
 
     if not args.no_batch and rank == 0:
+        line["parts"]["config0"] = time_config0(nrm, torch, ctx, dev)
         line["parts"].update(time_batch(nrm, torch, ctx, dev))
+        line["parts"]["config3"] = time_config3(nrm, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         hxd = xd.cpu().numpy()
         hxs = xs.cpu().numpy()
+        nproc = os.cpu_count() or 1
         t0 = time.perf_counter()
-        vd = oracle.nrm(hxd)
-        vs = oracle.nrm(hxs)
+        vd = oracle.nrm_par(hxd, threads=nproc)
+        vs = oracle.nrm_par(hxs, threads=nproc)
+        tp = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        vd1 = oracle.nrm(hxd)
+        vs1 = oracle.nrm(hxs)
         tc = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": (BYTES_D + BYTES_S) / tc / 1e9, "unit": "GB/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": "one full step (FP64 and FP32 vectors of 2^28), single thread, %.1f s" % tc,
-                                "bitwise_equal": bool(vd.tobytes() == np.float64(od.item()).tobytes()
-                                                      and vs.tobytes() == np.float32(os_.item()).tobytes())}
+        same = (vd.tobytes() == vd1.tobytes() == np.float64(od.item()).tobytes()
+                and vs.tobytes() == vs1.tobytes() == np.float32(os_.item()).tobytes())
+        line["cpu_baseline"] = {"value": (BYTES_D + BYTES_S) / tp / 1e9, "unit": "GB/s",
+                                "cores": 1 << max(0, (nproc - 1).bit_length()) if nproc > 1 else 1,
+                                "kind": "oracle", "nproc": nproc, "cpu_model": cpu_model(),
+                                "sample": "one full step (FP64 and FP32 vectors of 2^28) by the oracle's thread "
+                                          "driver (the top splits of the same tree on separate threads), %.2f s" % tp,
+                                "single_core": {"value": (BYTES_D + BYTES_S) / tc / 1e9, "unit": "GB/s",
+                                                "cores": 1, "seconds": tc},
+                                "bitwise_equal": bool(same)}
     if args.serve_seconds > 0 and rank == 0:
         del xd, xs
         torch.cuda.empty_cache()
-        line["parts"]["serve"] = time_serving(nrm, args.serve_seconds, args.serve_rate)
+        line["parts"]["serve"] = time_serving(nrm, args.serve_seconds, args.serve_rate, args.serve_baseline_seconds,
+                                              not args.no_saturation)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:

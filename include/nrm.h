@@ -195,44 +195,51 @@ nrm_status nrm_matrix(nrm_ctx *ctx, nrm_dtype dtype, const void *A, int64_t M, i
 /*
  * Ragged batch (the paper's per-column norms of Section 3.1, here for a
  * batch of independent vectors): for i in [0, B),
- *   out[i] = ||x[offsets[i] .. offsets[i+1])||_p
- * with the same tree as nrmp_* (p is rounded to the element type first).
+ *   out[i] = ||x[offsets[i] .. offsets[i+1])||_{p_i}
+ * with the same tree as nrmp_* (p_i is rounded to the element type first).
  *   x       : device pointer to x_len elements of `dtype`;
  *   offsets : device pointer to B+1 int64 element offsets (not bytes);
+ *   p       : the p of every vector when p_dev is NULL (xNRMP's p, Section 4);
+ *   p_dev   : NULL, or a device pointer to B doubles, p_i = p_dev[i] (p is
+ *             then ignored): one launch serves vectors with different p,
+ *             each combined with the combine nrmp_* takes for its p;
  *   out     : device pointer to B elements of `dtype`;
  *   status  : device pointer to B int32 (may be NULL): NRM_OK per vector,
- *             or NRM_EINVAL where offsets[i] < 0, offsets[i+1] < offsets[i]
- *             or offsets[i+1] > x_len -- that vector's out[i] is then NaN.
- *             Bad offsets are detected on the device; nothing traps.  If
- *             overlapping offsets would need more workspace than x_len
- *             implies, every vector reports NRM_ENOMEM (out NaN).
+ *             or NRM_EINVAL where offsets[i] < 0, offsets[i+1] < offsets[i],
+ *             offsets[i+1] > x_len, or p_dev[i] (rounded) is <= 0 or NaN --
+ *             that vector's out[i] is then NaN.  Bad offsets and p are
+ *             detected on the device; nothing traps.  If overlapping offsets
+ *             would need more workspace than x_len implies, every vector
+ *             reports NRM_ENOMEM (out NaN).
  * Work is distributed by a device-side plan and one persistent launch; every
- * out[i] is bitwise identical to nrmp_* on that vector alone.
+ * out[i] is bitwise identical to nrmp_* on that vector alone with p_i.
  * Errors (synchronous): NRM_EINVAL for bad dtype, B < 0, x_len < 0, NULL
- * offsets/out with B > 0, p <= 0 or NaN.
+ * offsets/out with B > 0, or (p_dev NULL) p <= 0 or NaN.
  */
 nrm_status nrm_batch(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
-                     int64_t B, double p, void *out, int32_t *status, void *stream);
+                     int64_t B, double p, const double *p_dev, void *out, int32_t *status, void *stream);
 
 /*
- * Batch of segments: out[i] = ||x[starts[i] .. starts[i] + lengths[i])||_p
- * (device arrays of B int64 each), the same tree and guarantees as
- * nrm_batch; segments may lie anywhere in x (a device arena) and in any
+ * Batch of segments: out[i] = ||x[starts[i] .. starts[i] + lengths[i])||_{p_i}
+ * (device arrays of B int64 each), the same tree, p / p_dev and guarantees
+ * as nrm_batch; segments may lie anywhere in x (a device arena) and in any
  * order.  A segment with starts[i] < 0, lengths[i] < 0 or starts[i] +
  * lengths[i] > x_len gives NaN and NRM_EINVAL in status[i].
  */
 nrm_status nrm_batch_segments(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *starts,
-                              const int64_t *lengths, int64_t B, double p, void *out, int32_t *status, void *stream);
+                              const int64_t *lengths, int64_t B, double p, const double *p_dev, void *out,
+                              int32_t *status, void *stream);
 
 /*
  * The same batch captured once into a CUDA graph (plan kernel + tree
  * kernel) and replayed with nrm_graph_launch; each replay reads the current
- * contents of x and offsets.  The context's workspace is sized for x_len and
- * B at capture time.  *graph receives an opaque handle owned by ctx.
+ * contents of x, offsets and p_dev (when not NULL).  The context's workspace
+ * is sized for x_len and B at capture time.  *graph receives an opaque
+ * handle owned by ctx.
  */
 typedef struct nrm_graph nrm_graph;
 nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
-                           int64_t B, double p, void *out, int32_t *status, nrm_graph **graph);
+                           int64_t B, double p, const double *p_dev, void *out, int32_t *status, nrm_graph **graph);
 nrm_status nrm_graph_launch(nrm_graph *graph, void *stream);
 nrm_status nrm_graph_destroy(nrm_graph *graph);
 
@@ -307,9 +314,9 @@ nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t *lengths_ho
  * time; a worker thread admits them in FIFO order as soon as their input
  * fits in the device arena, and launches steps on `nstreams` streams as
  * they free up, so steps overlap on the device and later arrivals join the
- * next step.  A step computes up to `max_batch` requests, grouped by (type,
- * p), with nrm_batch_segments; every result is bitwise the same as the
- * request computed alone.  The budget covers the input arena and the
+ * next step.  A step computes up to `max_batch` requests, grouped by element
+ * type, with one nrm_batch_segments per type (one p per request); every
+ * result is bitwise the same as the request computed alone.  The budget covers the input arena and the
  * streams' tree workspaces, which are reserved at creation (the loop never
  * allocates).  Latency is measured from arrival to the result on the host.
  */
@@ -332,6 +339,9 @@ typedef struct {
     int64_t peak_bytes, arena_bytes;
     double p50_ms, p99_ms, mean_ms, max_ms; /* arrival -> result on the host */
     double wall_s, norms_per_s, elements_per_s;
+    double host_launch_s; /* worker time spent issuing steps (copies, generator, plan and tree launches) */
+    double host_retire_s; /* worker time spent retiring finished steps */
+    double gpu_step_s;    /* sum over steps of their duration on the device (steps on several streams overlap) */
 } nrm_srv_report;
 
 /* Create a server on `device` with a device-memory budget (bytes, inputs +

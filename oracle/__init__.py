@@ -54,6 +54,8 @@ def lib():
             "or_Z_s": (None, [i64, vp, i32, f, vp]),
             "or_nrm_d": (d, [i64, vp, i32, d]),
             "or_nrm_s": (f, [i64, vp, i32, f]),
+            "or_nrm_par_d": (d, [i64, vp, i32, d, i32]),
+            "or_nrm_par_s": (f, [i64, vp, i32, f, i32]),
             "or_nrm_batch_d": (None, [i64, vp, vp, i32, d, vp]),
             "or_nrm_batch_s": (None, [i64, vp, vp, i32, f, vp]),
             "or_cr_hypot_d": (d, [d, d]),
@@ -212,6 +214,18 @@ def nrm(x, p=2.0, P=None):
         return np.float64(lib().or_nrm_d(a.size, ptr, P or P_D, float(p)))
     a, ptr = _arr(x, np.float32)
     return np.float32(lib().or_nrm_s(a.size, ptr, P or P_S, float(np.float32(p))))
+
+
+def nrm_par(x, p=2.0, threads=None, P=None):
+    """nrm() evaluated on `threads` host threads (default: all cores): the
+    top splits of the same tree run concurrently; bitwise equal to nrm()."""
+    import os
+    t = int(threads or os.cpu_count() or 1)
+    if _is_d(x):
+        a, ptr = _arr(x, np.float64)
+        return np.float64(lib().or_nrm_par_d(a.size, ptr, P or P_D, float(p), t))
+    a, ptr = _arr(x, np.float32)
+    return np.float32(lib().or_nrm_par_s(a.size, ptr, P or P_S, float(np.float32(p)), t))
 
 
 def cr_hypot(x, y, dtype=np.float64):

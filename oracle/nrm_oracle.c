@@ -29,6 +29,9 @@
  *   or_Z_*                 Z_x generalised to p lanes, Listing 4 (Section 3)
  *   or_nrm_*               xNRMF / xNRMP = Z then a final R over the lanes
  *                          (Section 3, recommendation for xNRMF)
+ *   or_nrm_par_*           the same on several threads (the top splits of
+ *                          Z evaluated concurrently, bitwise equal; used
+ *                          only to time the oracle on all host cores)
  *   or_cr_hypot_*          the correctly rounded hypot of the algorithm A
  *                          (Section 2), from its definition with integers
  *   or_nrm_za_*            Z then A for the final reduction (Section 3's
@@ -969,6 +972,93 @@ OR_API float or_nrm_s(int64_t n, const float *x, int P, float p)
     comb_s c = comb_for_s(p);
     float *f = (float *)malloc(sizeof(float) * (size_t)P);
     Z_s(n, x, P, &c, f);
+    const float v = R_s(P, f, &c);
+    free(f);
+    return v;
+}
+
+/* Thread driver (for timing the oracle on all host cores; Listing 4's
+ * OpenCilk spawn of the two halves): the same Z recursion in which the
+ * splits of the top `depth` levels evaluate their left part on a new thread
+ * while the current thread evaluates the right part.  The split points and
+ * the combine of the two halves are Z_d's, so the result is bitwise that of
+ * the serial recursion; only the order in which subtrees finish changes. */
+typedef struct { int64_t n; const double *x; int P; const comb_d *c; double *f; int depth; } zpar_d;
+typedef struct { int64_t n; const float *x; int P; const comb_s *c; float *f; int depth; } zpar_s;
+static void Z_par_d(int64_t n, const double *x, int P, const comb_d *c, double *f, int depth);
+static void Z_par_s(int64_t n, const float *x, int P, const comb_s *c, float *f, int depth);
+static void *zpar_thread_d(void *arg)
+{
+    const zpar_d *a = (const zpar_d *)arg;
+    Z_par_d(a->n, a->x, a->P, a->c, a->f, a->depth);
+    return NULL;
+}
+static void *zpar_thread_s(void *arg)
+{
+    const zpar_s *a = (const zpar_s *)arg;
+    Z_par_s(a->n, a->x, a->P, a->c, a->f, a->depth);
+    return NULL;
+}
+
+static void Z_par_d(int64_t n, const double *x, int P, const comb_d *c, double *f, int depth)
+{
+    const int64_t m = n / P + (n % P != 0);
+    if (depth <= 0 || m <= 2) { Z_d(n, x, P, c, f); return; }
+    const int64_t w = (m >> 1) + (m & 1);
+    const int64_t p = w * P;
+    double *g = (double *)malloc(sizeof(double) * (size_t)P);
+    zpar_d left = {p, x, P, c, f, depth - 1};
+    pthread_t th;
+    const int spawned = pthread_create(&th, NULL, zpar_thread_d, &left) == 0;
+    if (!spawned) Z_par_d(p, x, P, c, f, depth - 1);
+    Z_par_d(n - p, x + p, P, c, g, depth - 1);
+    if (spawned) pthread_join(th, NULL);
+    for (int l = 0; l < P; ++l) f[l] = comb_apply_d(c, f[l], g[l]);
+    free(g);
+}
+
+static void Z_par_s(int64_t n, const float *x, int P, const comb_s *c, float *f, int depth)
+{
+    const int64_t m = n / P + (n % P != 0);
+    if (depth <= 0 || m <= 2) { Z_s(n, x, P, c, f); return; }
+    const int64_t w = (m >> 1) + (m & 1);
+    const int64_t p = w * P;
+    float *g = (float *)malloc(sizeof(float) * (size_t)P);
+    zpar_s left = {p, x, P, c, f, depth - 1};
+    pthread_t th;
+    const int spawned = pthread_create(&th, NULL, zpar_thread_s, &left) == 0;
+    if (!spawned) Z_par_s(p, x, P, c, f, depth - 1);
+    Z_par_s(n - p, x + p, P, c, g, depth - 1);
+    if (spawned) pthread_join(th, NULL);
+    for (int l = 0; l < P; ++l) f[l] = comb_apply_s(c, f[l], g[l]);
+    free(g);
+}
+
+static int depth_for_threads(int nthreads)
+{
+    int d = 0;
+    while ((1 << d) < nthreads && d < 16) ++d;
+    return d;
+}
+
+/* or_nrm_* on up to 2^ceil(lg nthreads) threads, bitwise equal to it. */
+OR_API double or_nrm_par_d(int64_t n, const double *x, int P, double p, int nthreads)
+{
+    if (n <= 0) return 0.0;
+    comb_d c = comb_for_d(p);
+    double *f = (double *)malloc(sizeof(double) * (size_t)P);
+    Z_par_d(n, x, P, &c, f, depth_for_threads(nthreads));
+    const double v = R_d(P, f, &c);
+    free(f);
+    return v;
+}
+
+OR_API float or_nrm_par_s(int64_t n, const float *x, int P, float p, int nthreads)
+{
+    if (n <= 0) return 0.0f;
+    comb_s c = comb_for_s(p);
+    float *f = (float *)malloc(sizeof(float) * (size_t)P);
+    Z_par_s(n, x, P, &c, f, depth_for_threads(nthreads));
     const float v = R_s(P, f, &c);
     free(f);
     return v;

@@ -10,7 +10,8 @@ Entry points (same names as the C ABI):
 
 * ``nrmf(x)``           xNRMF of a 1-D float32/float64 CUDA tensor (0-d result on device)
 * ``nrmp(x, p)``        xNRMP, p > 0 (p = 2 is xNRMF, p = 1 sum |x|, p = inf max |x|)
-* ``nrm_batch(x, offsets, p)``       ragged batch -> (out, status)
+* ``nrm_batch(x, offsets, p)``       ragged batch -> (out, status); p a float or a
+                                     CUDA float64 tensor of one p per vector
 * ``nrm_batch_graph(...)``           the same, captured once as a CUDA graph
 * ``nrm_host(x_host, p)``            host buffer in, Python float out (end to end)
 * ``nrm_gen`` / ``nrm_gen_ragged``   seeded synthetic inputs on the device
@@ -52,7 +53,7 @@ class SrvReport(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "admitted", "rejected", "completed", "steps", "launches",
                                               "max_queue", "peak_bytes", "arena_bytes")] + \
                [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "wall_s", "norms_per_s",
-                                               "elements_per_s")]
+                                               "elements_per_s", "host_launch_s", "host_retire_s", "gpu_step_s")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -96,8 +97,8 @@ def load():
         "nrmf_es_s": (st, [vp, vp, i64, vp, vp]),
         "nrmf_es_d": (st, [vp, vp, i64, vp, vp]),
         "nrmp_d": (st, [vp, vp, i64, ctypes.c_double, vp, vp]),
-        "nrm_batch": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, vp]),
-        "nrm_batch_graph": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, ctypes.POINTER(vp)]),
+        "nrm_batch": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, vp, vp]),
+        "nrm_batch_graph": (st, [vp, i32, vp, i64, vp, i64, ctypes.c_double, vp, vp, vp, ctypes.POINTER(vp)]),
         "nrm_graph_launch": (st, [vp, vp]),
         "nrm_graph_destroy": (st, [vp]),
         "nrm_host": (st, [vp, i32, vp, i64, ctypes.c_double, vp]),
@@ -105,7 +106,7 @@ def load():
         "nrm_gen_ragged": (st, [i32, vp, i64, vp, i64, u64, i32, i32, vp]),
         "nrm_kernel_launches": (u64, [vp]),
         "nrm_autotune": (st, [vp, i32, vp, i64, ctypes.POINTER(Tuning)]),
-        "nrm_batch_segments": (st, [vp, i32, vp, i64, vp, vp, i64, ctypes.c_double, vp, vp, vp]),
+        "nrm_batch_segments": (st, [vp, i32, vp, i64, vp, vp, i64, ctypes.c_double, vp, vp, vp, vp]),
         "nrm_strided": (st, [vp, i32, vp, i64, i64, ctypes.c_double, vp, vp]),
         "nrm_matrix": (st, [vp, i32, vp, i64, i64, i64, ctypes.c_double, vp, vp]),
         "nrm_srv_create": (st, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
@@ -314,8 +315,20 @@ def nrmf_za(x, out=None, stream=None, ctx=None):
     return out
 
 
+def _p_args(p, B, device):
+    """(p, p_dev pointer): a scalar p for every vector, or a CUDA float64
+    tensor of B values, one p per vector (then the scalar is ignored)."""
+    import torch
+    if isinstance(p, torch.Tensor):
+        if p.dtype != torch.float64 or not p.is_cuda or p.numel() != B or not p.is_contiguous():
+            raise ValueError("a per-vector p must be a contiguous float64 CUDA tensor of B values")
+        return 2.0, ctypes.c_void_p(p.data_ptr() if B else 0)
+    return float(p), None
+
+
 def nrm_batch(x, offsets, p=2.0, out=None, status=None, stream=None, ctx=None):
-    """Norms of x[offsets[i]:offsets[i+1]] for all i; returns (out, status)."""
+    """Norms of x[offsets[i]:offsets[i+1]] for all i; returns (out, status).
+    p: one value for all vectors, or a float64 CUDA tensor of one per vector."""
     import torch
     _check_vec(x)
     dt = _dtype_code(x)
@@ -327,8 +340,9 @@ def nrm_batch(x, offsets, p=2.0, out=None, status=None, stream=None, ctx=None):
         out = torch.empty(max(B, 0), dtype=x.dtype, device=x.device)
     if status is None:
         status = torch.empty(max(B, 0), dtype=torch.int32, device=x.device)
+    ps, pd = _p_args(p, B, x.device)
     r = load().nrm_batch(c.h, dt, ctypes.c_void_p(x.data_ptr() if x.numel() else 0), x.numel(),
-                         ctypes.c_void_p(offsets.data_ptr()), B, float(p), ctypes.c_void_p(out.data_ptr()),
+                         ctypes.c_void_p(offsets.data_ptr()), B, ps, pd, ctypes.c_void_p(out.data_ptr()),
                          ctypes.c_void_p(status.data_ptr()), _stream(stream))
     c.check(r, "nrm_batch")
     return out, status
@@ -347,8 +361,10 @@ class BatchGraph:
         self.out = out if out is not None else torch.empty(B, dtype=x.dtype, device=x.device)
         self.status = status if status is not None else torch.empty(B, dtype=torch.int32, device=x.device)
         h = ctypes.c_void_p()
+        ps, pd = _p_args(p, B, x.device)
+        self.p = p  # a per-vector p tensor is read by every replay
         r = load().nrm_batch_graph(self.ctx.h, dt, ctypes.c_void_p(x.data_ptr()), x.numel(),
-                                   ctypes.c_void_p(offsets.data_ptr()), B, float(p),
+                                   ctypes.c_void_p(offsets.data_ptr()), B, ps, pd,
                                    ctypes.c_void_p(self.out.data_ptr()), ctypes.c_void_p(self.status.data_ptr()),
                                    ctypes.byref(h))
         self.ctx.check(r, "nrm_batch_graph")
@@ -429,9 +445,10 @@ def nrm_batch_segments(x, starts, lengths, p=2.0, out=None, status=None, stream=
         out = torch.empty(B, dtype=x.dtype, device=x.device)
     if status is None:
         status = torch.empty(B, dtype=torch.int32, device=x.device)
+    ps, pd = _p_args(p, B, x.device)
     r = load().nrm_batch_segments(c.h, dt, ctypes.c_void_p(x.data_ptr()), x.numel(),
                                   ctypes.c_void_p(starts.data_ptr()), ctypes.c_void_p(lengths.data_ptr()), B,
-                                  float(p), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                                  ps, pd, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(status.data_ptr()),
                                   _stream(stream))
     c.check(r, "nrm_batch_segments")
     return out, status
@@ -529,10 +546,24 @@ def serving_trace(rate, seconds, seed=0, min_log2=4, max_log2=24, p_probs=(0.8, 
     cp = np.cumsum(p_probs)
     pidx = np.searchsorted(cp, u[:m, 3] * cp[-1], side="right")
     pv = np.asarray(ps, np.float64)[np.minimum(pidx, len(ps) - 1)]
-    arr = (Request * m)()
-    for i in range(m):
-        arr[i] = Request(int(dts[i]), -20, 20, float(pv[i]), int(L[i]), None, int(seed), float(t[i]))
-    return arr
+    rec = np.zeros(m, dtype=request_dtype())
+    rec["dtype"], rec["emin"], rec["emax"] = dts, -20, 20
+    rec["p"], rec["n"], rec["seed"], rec["arrival_s"] = pv, L, seed, t[:m]
+    return (Request * m).from_buffer(rec)  # shares (and keeps alive) rec's memory
+
+
+def request_dtype():
+    """numpy record layout of the C struct nrm_request (same offsets)."""
+    names = [f for f, _ in Request._fields_]
+    fmt = {ctypes.c_int32: np.int32, ctypes.c_double: np.float64, ctypes.c_int64: np.int64,
+           ctypes.c_void_p: np.uint64, ctypes.c_uint64: np.uint64}
+    return np.dtype({"names": names, "formats": [fmt[t] for _, t in Request._fields_],
+                     "offsets": [getattr(Request, f).offset for f in names], "itemsize": ctypes.sizeof(Request)})
+
+
+def trace_records(reqs):
+    """A numpy record view of a ctypes array of Request (no copy)."""
+    return np.frombuffer(reqs, dtype=request_dtype())
 
 
 def nrm_strided(buf, n, incx, p=2.0, out=None, stream=None, ctx=None):

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libnrm.so")
-SOURCES = ["nrm_kernels.cu", "nrm_runtime.cu", "nrm_gen.cu", "nrm_serve.cu", "nrm_probe.cu"]
+SOURCES = ["nrm_tree_d.cu", "nrm_tree_s.cu", "nrm_tree_mixed.cu", "nrm_kernels.cu", "nrm_runtime.cu", "nrm_gen.cu",
+           "nrm_serve.cu", "nrm_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",

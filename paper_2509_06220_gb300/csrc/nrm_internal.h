@@ -46,7 +46,7 @@ nrm_status nrm_plan_single(const nrm_ctx *c, nrm_dtype dt, int64_t n, nrm::VecPl
 nrm_status nrm_run_single_range(nrm_ctx *c, nrm_dtype dt, const void *x, int64_t n, double p, void *out,
                                 cudaStream_t s, const nrm::VecPlan *pl, int64_t item_lo, int64_t item_hi);
 nrm_status nrm_batch_impl(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
-                          int64_t B, double p, void *out, int32_t *status, cudaStream_t s,
+                          int64_t B, double p, const double *p_dev, void *out, int32_t *status, cudaStream_t s,
                           const int64_t *lens = nullptr);
 size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);
 int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);

@@ -37,11 +37,11 @@ void nrm_graph_free(nrm_graph *g) {
 }
 
 extern "C" nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len,
-                                      const int64_t *offsets, int64_t B, double p, void *out, int32_t *status,
-                                      nrm_graph **graph) {
+                                      const int64_t *offsets, int64_t B, double p, const double *p_dev, void *out,
+                                      int32_t *status, nrm_graph **graph) {
     if (!ctx || !graph) return NRM_EINVAL;
     *graph = nullptr;
-    if (B <= 0 || !offsets || !out || x_len < 0 || (x_len > 0 && !x) || !(p > 0.0) ||
+    if (B <= 0 || !offsets || !out || x_len < 0 || (x_len > 0 && !x) || (!p_dev && !(p > 0.0)) ||
         (dtype != NRM_F32 && dtype != NRM_F64))
         return NRM_EINVAL;
     nrm_status st = nrm_ctx_ensure(ctx, nrm_batch_ws_bytes(ctx, dtype, x_len, B), nrm_batch_tickets(ctx, dtype, x_len, B));
@@ -55,7 +55,7 @@ extern "C" nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void 
     nrm_graph *g = new nrm_graph{ctx, nullptr, nullptr};
     e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        st = nrm_batch_impl(ctx, dtype, x, x_len, offsets, B, p, out, status, s);
+        st = nrm_batch_impl(ctx, dtype, x, x_len, offsets, B, p, p_dev, out, status, s);
         cudaError_t e2 = cudaStreamEndCapture(s, &g->graph);
         if (st == NRM_OK && e2 != cudaSuccess) e = e2;
     }
@@ -243,7 +243,7 @@ extern "C" nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t 
     float best_ms = 1e30f;
     auto run = [&](void) -> nrm_status {
         if (B == 1) return nrm_run_single_range(ctx, dtype, x, total, 2.0, out, s, nullptr, 0, 0);
-        return nrm_batch_impl(ctx, dtype, x, total, offd, B, 2.0, out, nullptr, s);
+        return nrm_batch_impl(ctx, dtype, x, total, offd, B, 2.0, nullptr, out, nullptr, s);
     };
     for (int G = 2; G <= 3 && st == NRM_OK; ++G)
         for (int wpb : {4, 8, 16})

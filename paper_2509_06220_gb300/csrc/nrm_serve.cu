@@ -6,10 +6,11 @@
 //   -> launch the next step on every idle stream,
 // so requests that arrive while others are on the GPU join the next step as
 // soon as memory frees up, and steps on different streams overlap on the
-// device.  A step groups its requests by (element type, p) and computes each
-// group with one segment batch (nrm_batch_segments) over the request inputs,
-// which live in one device arena: every result is bitwise the result of the
-// same request computed alone (the tree depends on the vector only).
+// device.  A step groups its requests by element type and computes each
+// group with one segment batch (nrm_batch_segments, with one p per request
+// when the group's p differ) over the request inputs, which live in one
+// device arena: every result is bitwise the result of the same request
+// computed alone (the tree depends on the vector and its p only).
 //
 // Memory: the budget covers the arena (inputs) and each stream's tree
 // workspace, which is reserved up front so the loop never allocates.  A
@@ -103,6 +104,8 @@ struct Lane {
     nrm_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr; // timing: start and end of the step on the device
+    double *h_p = nullptr, *d_p = nullptr;  // per-request p of a step (groups with mixed p)
     int64_t *h_starts = nullptr, *h_lens = nullptr, *d_starts = nullptr, *d_lens = nullptr;
     double *h_out = nullptr, *d_out = nullptr; // results widened per group slot (8 bytes each)
     int32_t *h_status = nullptr, *d_status = nullptr;
@@ -130,6 +133,8 @@ struct nrm_srv {
     std::atomic<bool> stop{false};
     // statistics
     int64_t submitted = 0, rejected = 0, completed = 0; // under mu
+    int64_t finished = 0;                               // under mu: requests done (completed or failed)
+    double host_launch_s = 0, host_retire_s = 0, gpu_step_s = 0; // worker-written, read under mu
     std::atomic<int64_t> steps{0}, launches{0}, elements{0}, peak_bytes{0}; // worker-written
     int64_t max_queue = 0;
     std::vector<double> lat_ms;
@@ -144,6 +149,8 @@ namespace {
 // lane's d_out slots; widen them to double on the host
 void retire(nrm_srv *s, Lane &ln) {
     const clk::time_point now = clk::now();
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ln.t0, ln.t1) == cudaSuccess) s->gpu_step_s += ms * 1e-3;
     for (size_t i = 0; i < ln.batch.size(); ++i) {
         Req *q = ln.batch[i];
         const char *src = (const char *)ln.h_out + q->res_byte;
@@ -158,11 +165,13 @@ void retire(nrm_srv *s, Lane &ln) {
         q->done = true;
         if (q->off >= 0) s->arena.release((size_t)q->off, req_bytes(q));
         s->completed++;
+        s->finished++;
         s->lat_ms.push_back(secs(q->t_arrival, now) * 1e3);
         s->t_last = now;
     }
     ln.batch.clear();
     ln.busy = false;
+    s->host_retire_s += secs(now, clk::now());
     s->cv_done.notify_all();
 }
 
@@ -171,11 +180,10 @@ nrm_status launch_step(nrm_srv *s, Lane &ln) {
     const size_t take = std::min(s->admitted.size(), (size_t)s->max_batch);
     ln.batch.assign(s->admitted.begin(), s->admitted.begin() + take);
     s->admitted.erase(s->admitted.begin(), s->admitted.begin() + take);
-    // order by (type, p) so that each group is a contiguous slot range
-    std::stable_sort(ln.batch.begin(), ln.batch.end(), [](const Req *a, const Req *b) {
-        if (a->r.dtype != b->r.dtype) return a->r.dtype < b->r.dtype;
-        return a->r.p < b->r.p;
-    });
+    // order by type so that each group is a contiguous slot range
+    std::stable_sort(ln.batch.begin(), ln.batch.end(),
+                     [](const Req *a, const Req *b) { return a->r.dtype < b->r.dtype; });
+    if (cudaEventRecord(ln.t0, ln.stream) != cudaSuccess) return NRM_ECUDA;
     const size_t B = ln.batch.size();
     int64_t ng = 0, gtotal = 0;
     for (size_t i = 0; i < B; ++i) {
@@ -183,6 +191,7 @@ nrm_status launch_step(nrm_srv *s, Lane &ln) {
         const size_t es = elem_size(q->r.dtype);
         ln.h_starts[i] = q->r.n > 0 ? q->off / (int64_t)es : 0;
         ln.h_lens[i] = q->r.n;
+        ln.h_p[i] = q->r.p;
         s->elements += q->r.n;
         if (q->r.n == 0) continue;
         if (q->r.x_host) {
@@ -204,7 +213,8 @@ nrm_status launch_step(nrm_srv *s, Lane &ln) {
     }
     if (cudaMemcpyAsync(ln.d_starts, ln.h_starts, B * sizeof(int64_t), cudaMemcpyHostToDevice, ln.stream) !=
             cudaSuccess ||
-        cudaMemcpyAsync(ln.d_lens, ln.h_lens, B * sizeof(int64_t), cudaMemcpyHostToDevice, ln.stream) != cudaSuccess)
+        cudaMemcpyAsync(ln.d_lens, ln.h_lens, B * sizeof(int64_t), cudaMemcpyHostToDevice, ln.stream) != cudaSuccess ||
+        cudaMemcpyAsync(ln.d_p, ln.h_p, B * sizeof(double), cudaMemcpyHostToDevice, ln.stream) != cudaSuccess)
         return NRM_ECUDA;
     if (ng > 0) {
         if (cudaMemcpyAsync(ln.d_segs, ln.h_segs, (size_t)ng * sizeof(NrmGenSeg), cudaMemcpyHostToDevice, ln.stream) !=
@@ -218,8 +228,11 @@ nrm_status launch_step(nrm_srv *s, Lane &ln) {
     size_t g0 = 0;
     while (g0 < B) {
         size_t g1 = g0 + 1;
-        while (g1 < B && ln.batch[g1]->r.dtype == ln.batch[g0]->r.dtype && ln.batch[g1]->r.p == ln.batch[g0]->r.p)
+        bool one_p = true; // every request of the group has the same p: no per-vector p needed
+        while (g1 < B && ln.batch[g1]->r.dtype == ln.batch[g0]->r.dtype) {
+            one_p = one_p && ln.batch[g1]->r.p == ln.batch[g0]->r.p;
             ++g1;
+        }
         const nrm_dtype dt = ln.batch[g0]->r.dtype;
         const size_t es = elem_size(dt);
         // the group's results are packed values of type dt starting at byte
@@ -227,7 +240,8 @@ nrm_status launch_step(nrm_srv *s, Lane &ln) {
         for (size_t j = g0; j < g1; ++j) ln.batch[j]->res_byte = g0 * 8 + (j - g0) * es;
         nrm_status st = nrm_batch_segments(ln.ctx, dt, s->arena_ptr, (int64_t)(s->arena_bytes / es),
                                            ln.d_starts + g0, ln.d_lens + g0, (int64_t)(g1 - g0), ln.batch[g0]->r.p,
-                                           (char *)ln.d_out + g0 * 8, ln.d_status + g0, ln.stream);
+                                           one_p ? nullptr : ln.d_p + g0, (char *)ln.d_out + g0 * 8,
+                                           ln.d_status + g0, ln.stream);
         if (st != NRM_OK) return st;
         s->launches += 2;
         g0 = g1;
@@ -235,7 +249,7 @@ nrm_status launch_step(nrm_srv *s, Lane &ln) {
     if (cudaMemcpyAsync(ln.h_out, ln.d_out, B * 8, cudaMemcpyDeviceToHost, ln.stream) != cudaSuccess ||
         cudaMemcpyAsync(ln.h_status, ln.d_status, B * sizeof(int32_t), cudaMemcpyDeviceToHost, ln.stream) !=
             cudaSuccess ||
-        cudaEventRecord(ln.ev, ln.stream) != cudaSuccess)
+        cudaEventRecord(ln.t1, ln.stream) != cudaSuccess || cudaEventRecord(ln.ev, ln.stream) != cudaSuccess)
         return NRM_ECUDA;
     ln.busy = true;
     s->steps++;
@@ -281,7 +295,13 @@ void worker_loop(nrm_srv *s) {
         }
         for (Lane &ln : s->lanes) {
             if (!ln.busy && !s->admitted.empty()) {
+                const clk::time_point h0 = clk::now();
                 nrm_status st = launch_step(s, ln);
+                const double hs = secs(h0, clk::now());
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    s->host_launch_s += hs;
+                }
                 if (st != NRM_OK) {
                     std::lock_guard<std::mutex> lk(s->mu);
                     s->fatal = st;
@@ -289,6 +309,7 @@ void worker_loop(nrm_srv *s) {
                         q->status = st;
                         q->done = true;
                         q->t_done = clk::now();
+                        s->finished++;
                     }
                     ln.batch.clear();
                     s->cv_done.notify_all();
@@ -333,6 +354,9 @@ extern "C" nrm_status nrm_srv_create(nrm_srv **srv, int device, size_t budget_by
         reserved += ws + (size_t)tk * 4;
         if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&ln.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&ln.t0) != cudaSuccess || cudaEventCreate(&ln.t1) != cudaSuccess ||
+            cudaMallocHost(&ln.h_p, (size_t)max_batch * 8) != cudaSuccess ||
+            cudaMalloc(&ln.d_p, (size_t)max_batch * 8) != cudaSuccess ||
             cudaMallocHost(&ln.h_starts, (size_t)max_batch * 8) != cudaSuccess ||
             cudaMallocHost(&ln.h_lens, (size_t)max_batch * 8) != cudaSuccess ||
             cudaMallocHost(&ln.h_out, (size_t)max_batch * 8) != cudaSuccess ||
@@ -349,7 +373,7 @@ extern "C" nrm_status nrm_srv_create(nrm_srv **srv, int device, size_t budget_by
             st = NRM_ENOMEM;
             break;
         }
-        reserved += (size_t)max_batch * (20 + 8 + sizeof(NrmGenSeg));
+        reserved += (size_t)max_batch * (20 + 8 + 8 + sizeof(NrmGenSeg));
     }
     if (st == NRM_OK) {
         if (reserved + (1u << 20) > budget_bytes) st = NRM_EBUDGET; // no room left for inputs
@@ -381,6 +405,10 @@ extern "C" nrm_status nrm_srv_destroy(nrm_srv *s) {
     cudaDeviceSynchronize();
     for (Lane &ln : s->lanes) {
         if (ln.ev) cudaEventDestroy(ln.ev);
+        if (ln.t0) cudaEventDestroy(ln.t0);
+        if (ln.t1) cudaEventDestroy(ln.t1);
+        if (ln.h_p) cudaFreeHost(ln.h_p);
+        if (ln.d_p) cudaFree(ln.d_p);
         if (ln.stream) cudaStreamDestroy(ln.stream);
         if (ln.h_starts) cudaFreeHost(ln.h_starts);
         if (ln.h_lens) cudaFreeHost(ln.h_lens);
@@ -446,10 +474,7 @@ extern "C" nrm_status nrm_srv_drain(nrm_srv *s, double timeout_s) {
     if (!s) return NRM_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     const auto deadline = clk::now() + std::chrono::duration_cast<clk::duration>(std::chrono::duration<double>(timeout_s));
-    while (s->completed + (int64_t)0 < (int64_t)s->reqs.size()) {
-        bool all = true;
-        for (auto &kv : s->reqs) all = all && kv.second->done;
-        if (all) break;
+    while (s->finished < (int64_t)s->reqs.size()) {
         if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) return NRM_ETIMEOUT;
     }
     return s->fatal;
@@ -468,6 +493,9 @@ extern "C" nrm_status nrm_srv_report_get(nrm_srv *s, nrm_srv_report *rep) {
     rep->max_queue = s->max_queue;
     rep->peak_bytes = s->peak_bytes.load();
     rep->arena_bytes = (int64_t)s->arena_bytes;
+    rep->host_launch_s = s->host_launch_s;
+    rep->host_retire_s = s->host_retire_s;
+    rep->gpu_step_s = s->gpu_step_s;
     std::vector<double> v = s->lat_ms;
     if (!v.empty()) {
         std::sort(v.begin(), v.end());

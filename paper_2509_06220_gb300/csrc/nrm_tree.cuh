@@ -1,0 +1,739 @@
+// nrm_tree.cuh -- the xNRMF / xNRMP tree kernels for sm_103a, their batch
+// planner and their host-side launchers (arXiv 2509.06220, Listings 1, 2, 4,
+// 5).  Internal: the kernels of each element type are instantiated in their
+// own translation unit (nrm_tree_d.cu, nrm_tree_s.cu; the batch kernel with
+// one p per vector in nrm_tree_mixed.cu), and nrm_kernels.cu calls them
+// through run_single_x / run_batch_x.
+//
+//
+// Mapping of the paper's vectorised recursion onto the GPU
+// ---------------------------------------------------------
+// * A vector's elements form rows of P lanes (P = 64 for binary64, 128 for
+//   binary32; one 512-byte row).  One warp holds one row in registers: thread
+//   t owns lanes [V t, V t + V), loaded with one 16-byte load.
+// * The ceil-split tree over the m rows (Listing 4's recursion on vectors)
+//   is embedded in a perfect tree of depth D = ceil(lg m): slot j holds a
+//   row iff brev_D(j) < m; a node with an empty child passes the other
+//   through, so the embedding computes exactly Listing 4's tree.
+// * The tree is cut at depth dw into 2^dw work items; a warp evaluates one
+//   item (a subtree of 2^k slots) with groups of 2^G slots combined in
+//   registers and a binary-counter stack above them.
+// * Above the cut, each internal node has a ticket.  The warp that finishes a
+//   child stores its 512-byte row of partial norms, fences, and increments
+//   the parent's ticket; the second arriver combines the two children (left
+//   operand = left child) and climbs on.  Whoever combines the root reduces
+//   the P lanes with R's contiguous pairing (in-thread, then warp shuffles)
+//   and writes the result.  The arrival order never changes a bit.
+// * The second arriver resets the ticket, so tickets are zero between calls.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nrm.h"
+#include "nrm_device.cuh"
+#include "nrm_internal.h"
+
+namespace nrm {
+
+// ---------------------------------------------------------------------------
+// kernel arguments
+// ---------------------------------------------------------------------------
+template <typename T> struct TreeArgs {
+    const T *x;
+    T *out;
+    const VecPlan *plans; // batch: device plans; nullptr: single vector `one`
+    VecPlan one;
+    int64_t B;
+    int64_t item_lo, item_hi;      // single vector: item range of this launch
+    const int64_t *total_items;    // batch: written by the plan kernel
+    unsigned long long *cursor;    // batch: dynamic work cursor (zeroed by plan)
+    unsigned *tickets;
+    T *slots;
+    int levels;                    // counter-stack rows per warp: max k - G of the launch
+};
+
+// R over the P lanes held by the warp (Listing 1 with contiguous pairing):
+// first inside the thread, then across threads by xor-shuffles.
+template <typename T, class Op>
+__device__ __forceinline__ T lane_reduce(const T (&r)[Geo<T>::V], const Op &op, int lane) {
+    T v;
+    if constexpr (Geo<T>::V == 2) {
+        v = op(r[0], r[1]);
+    } else {
+        v = op(op(r[0], r[1]), op(r[2], r[3]));
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T o = __shfl_xor_sync(FULL, v, off);
+        v = (lane & off) ? op(o, v) : op(v, o);
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row(T *dst, const T (&r)[Geo<T>::V]) {
+    if constexpr (Geo<T>::V == 2) {
+        __stcg(reinterpret_cast<double2 *>(dst), make_double2(r[0], r[1]));
+    } else {
+        __stcg(reinterpret_cast<float4 *>(dst), make_float4(r[0], r[1], r[2], r[3]));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_slot(const T *src, T (&r)[Geo<T>::V]) {
+    if constexpr (Geo<T>::V == 2) {
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(src));
+        r[0] = v.x;
+        r[1] = v.y;
+    } else {
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(src));
+        r[0] = v.x;
+        r[1] = v.y;
+        r[2] = v.z;
+        r[3] = v.w;
+    }
+}
+
+// The register cap comes from the combine (Op::kMaxRegs): the trees are
+// latency-bound, so more resident warps pay more than per-thread ILP (a
+// sweep on GB300 found 64 registers best for v1_hypot in both precisions).
+// FinalA: reduce the P lane partials with the correctly rounded hypot (the
+// algorithm A; Z with A is the paper's recommended xNRMF) instead of op.
+// stages of the cp.async ring of work items (Op::kStages, default none)
+template <class Op, class = void> struct StagesOf {
+    static constexpr int value = 0;
+};
+template <class Op> struct StagesOf<Op, std::void_t<decltype(Op::kStages)>> {
+    static constexpr int value = Op::kStages;
+};
+
+// dynamic shared memory of a tree block: per warp, the counter stack of
+// `levels` rows (k - G for the deepest work item of the launch, at most
+// MAXL) and the ring of StagesOf<Op> groups of 2^G rows (512 bytes a row)
+template <int G, class Op> constexpr size_t tree_smem_bytes(int wpb, int levels) {
+    return (size_t)wpb * ((size_t)levels * 512 + (size_t)StagesOf<Op>::value * (1u << G) * 512);
+}
+
+// stack rows for work items of at most 2^kmax rows
+static int stack_levels(int kmax, int G) { return std::max(0, std::min(MAXL, kmax - G)); }
+
+// One work item: global item gi, the item's subtree (index gi - item_base
+// at depth dw of vector v's row tree, plan pl), the climb of the ticket tree
+// above the cut, and -- for whoever combines the root -- the lane reduction
+// and the store of the result.
+// stk: this warp's counter stack; ring: its cp.async ring (ops with stages).
+template <typename T, int G, class Op, bool FinalA>
+__device__ __forceinline__ void process_item(const TreeArgs<T> &a, const VecPlan &pl, int64_t v, int64_t gi,
+                                             int lane, bool batch, const Op &op, T *stk,
+                                             typename Geo<T>::vec *ring) {
+    constexpr int V = Geo<T>::V;
+    constexpr int P = Geo<T>::P;
+    constexpr int NS = StagesOf<Op>::value;
+    const T *xv = a.x + pl.x_off;
+    const bool aligned = pl.stride == 1 && ((uintptr_t)xv & 15u) == 0;
+    const uint32_t i = (uint32_t)(gi - pl.item_base);
+    const int64_t t = node_rows(pl.m, i, pl.dw);
+    const int64_t start = node_start(pl.m, i, pl.dw);
+    T r[V];
+    bool done = false;
+    if constexpr (NS > 0) {
+        if (pl.stride == 1 && pl.k > G && t >= (int64_t(1) << (pl.k - G))) {
+            const bool tail = (start + t) * P > pl.n;
+            if (t == (int64_t(1) << pl.k)) {
+                if (aligned)
+                    done = item_tree_async<T, G, Op, NS, true, 1>(xv, pl.n, start, t, pl.k, lane, true, tail, op,
+                                                                  stk, ring, r);
+                else
+                    done = item_tree_async<T, G, Op, NS, true, 0>(xv, pl.n, start, t, pl.k, lane, false, tail, op,
+                                                                  stk, ring, r);
+            } else {
+                done = item_tree_async<T, G, Op, NS, false, -1>(xv, pl.n, start, t, pl.k, lane, aligned, tail, op,
+                                                                stk, ring, r);
+            }
+        }
+    }
+    if (!done) item_tree<T, G, Op>(xv, pl.n, start, t, pl.k, lane, aligned, pl.stride, op, stk, r);
+
+    // climb the ticket tree above the cut
+    uint32_t h = (1u << pl.dw) + i;
+    bool root = true;
+    while (h > 1) {
+        T *mine = a.slots + ((size_t)(2 * pl.node_base + h - 2) * P) + lane * V;
+        store_row<T>(mine, r);
+        __threadfence();
+        __syncwarp();
+        unsigned tk = 0;
+        unsigned *ticket = a.tickets + (pl.node_base + (h >> 1) - 1);
+        if (lane == 0) tk = atomicAdd(ticket, 1u);
+        tk = __shfl_sync(FULL, tk, 0);
+        if (tk == 0) {
+            root = false; // the sibling is still running; it climbs on
+            break;
+        }
+        if (lane == 0) atomicExch(ticket, 0u);
+        __threadfence();
+        T sib[V];
+        load_slot<T>(a.slots + ((size_t)(2 * pl.node_base + (h ^ 1u) - 2) * P) + lane * V, sib);
+        if (h & 1u) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) r[j] = op(sib[j], r[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) r[j] = op(r[j], sib[j]);
+        }
+        h >>= 1;
+    }
+    if (root) {
+        T res;
+        if constexpr (FinalA) res = lane_reduce<T, OpCrHypot<T>>(r, OpCrHypot<T>{}, lane);
+        else res = lane_reduce<T, Op>(r, op, lane);
+        if (lane == 0) a.out[batch ? pl.out_idx : v] = res;
+    }
+}
+
+// the plan of the vector owning global item gi (last v with item_base <= gi)
+template <typename T> __device__ __forceinline__ int64_t owner_of(const TreeArgs<T> &a, int64_t gi) {
+    int64_t lo = 0, hi = a.B;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a.plans[mid].item_base <= gi) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// this warp's counter stack (a.levels rows) and ring (NS groups of 2^G rows)
+// in the block's dynamic shared memory: all stacks first, then the rings
+template <typename T, int G, int NS>
+__device__ __forceinline__ void warp_smem(const TreeArgs<T> &a, T *&stk, typename Geo<T>::vec *&ring) {
+    extern __shared__ __align__(16) unsigned char nrm_smem[];
+    stk = reinterpret_cast<T *>(nrm_smem) + (threadIdx.x >> 5) * (a.levels * Geo<T>::P);
+    ring = reinterpret_cast<typename Geo<T>::vec *>(nrm_smem + (size_t)(blockDim.x >> 5) * a.levels * 512 +
+                                                    (size_t)(threadIdx.x >> 5) * (NS * (1u << G) * 512));
+}
+
+template <typename T, int G, class Op, bool FinalA = false>
+__global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wglobal = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool batch = a.plans != nullptr;
+    const int64_t total = batch ? *a.total_items : a.item_hi;
+    T *stk;
+    typename Geo<T>::vec *ring;
+    warp_smem<T, G, StagesOf<Op>::value>(a, stk, ring);
+
+    int64_t gi;
+    if (batch) {
+        unsigned long long g0 = 0;
+        if (lane == 0) g0 = atomicAdd(a.cursor, 1ull);
+        gi = (int64_t)__shfl_sync(FULL, g0, 0);
+    } else {
+        gi = a.item_lo + wglobal;
+    }
+    while (gi < total) {
+        int64_t v = 0;
+        VecPlan pl;
+        if (batch) {
+            v = owner_of<T>(a, gi);
+            pl = a.plans[v];
+        } else {
+            pl = a.one;
+        }
+        process_item<T, G, Op, FinalA>(a, pl, v, gi, lane, batch, op, stk, ring);
+        if (batch) {
+            unsigned long long g1 = 0;
+            if (lane == 0) g1 = atomicAdd(a.cursor, 1ull);
+            gi = (int64_t)__shfl_sync(FULL, g1, 0);
+        } else {
+            gi += nwarps;
+        }
+    }
+}
+
+// A ragged batch with a p per vector: the same persistent loop, each work
+// item combined with its vector's op (a warp-uniform switch: an item belongs
+// to one vector), so every result is bitwise that of the single-p kernel for
+// that vector's p.  The register cap is the largest of the ops' caps (v1_lp).
+template <typename T, int G>
+__global__ void __maxnreg__(OpLp<T>::kMaxRegs) tree_kernel_mixed(TreeArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = *a.total_items;
+    T *stk;
+    typename Geo<T>::vec *ring; // sized for the largest ring of the ops (v1_hypot's)
+    warp_smem<T, G, StagesOf<OpHypot<T>>::value>(a, stk, ring);
+    unsigned long long g0 = 0;
+    if (lane == 0) g0 = atomicAdd(a.cursor, 1ull);
+    int64_t gi = (int64_t)__shfl_sync(FULL, g0, 0);
+    while (gi < total) {
+        const int64_t v = owner_of<T>(a, gi);
+        const VecPlan pl = a.plans[v];
+        switch (pl.op) {
+        case OP_HYPOT:
+            process_item<T, G, OpHypot<T>, false>(a, pl, v, gi, lane, true, OpHypot<T>{}, stk, ring);
+            break;
+        case OP_LP: {
+            OpLp<T> o;
+            o.h = (T)pl.h;
+            o.ip = (T)pl.ip;
+            process_item<T, G, OpLp<T>, false>(a, pl, v, gi, lane, true, o, stk, ring);
+            break;
+        }
+        case OP_SUMABS:
+            process_item<T, G, OpSumAbs<T>, false>(a, pl, v, gi, lane, true, OpSumAbs<T>{}, stk, ring);
+            break;
+        default: process_item<T, G, OpMaxAbs<T>, false>(a, pl, v, gi, lane, true, OpMaxAbs<T>{}, stk, ring); break;
+        }
+        unsigned long long g1 = 0;
+        if (lane == 0) g1 = atomicAdd(a.cursor, 1ull);
+        gi = (int64_t)__shfl_sync(FULL, g1, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// batch planning (one block): offsets -> per-vector plans, prefix sums of
+// work items and ticket nodes, statuses, outputs of empty / bad vectors, and
+// the reset of the work cursor
+// ---------------------------------------------------------------------------
+// Vector v is x[off[v] .. off[v+1]) when lens == nullptr (consecutive
+// vectors), else the segment x[off[v] .. off[v] + lens[v]).
+// Per-vector p (pdev != nullptr): vector v's p is pdev[v] rounded to T;
+// its combine follows the rule of one p per call (Section 4): 2 -> v1_hypot,
+// 1 -> sumabs, at or above the cut-off p' -> maxabs, otherwise v1_lp with
+// h = p/2 and ip = 1/p rounded in T; p <= 0 or NaN is NRM_EINVAL.
+template <typename T> __device__ __forceinline__ bool plan_op(double pd, VecPlan &pl) {
+    const T p = (T)pd;
+    if (!(p > T(0))) return false;
+    const T cut = sizeof(T) == 8 ? T(9007199254740992.0) : T(16777216.0f);
+    pl.h = 0.0;
+    pl.ip = 0.0;
+    if (p == T(2)) pl.op = OP_HYPOT;
+    else if (p == T(1)) pl.op = OP_SUMABS;
+    else if (p >= cut) pl.op = OP_MAXABS;
+    else {
+        pl.op = OP_LP;
+        pl.h = (double)rmul(p, T(0.5));
+        pl.ip = (double)rdiv(T(1), p);
+    }
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ off, const int64_t *__restrict__ lens,
+                                                    const double *__restrict__ pdev, int64_t B, int64_t x_len,
+                                                    int kitem, int dwmax, int kmax, int64_t node_cap,
+                                                    VecPlan *plans, int64_t *totals, unsigned long long *cursor,
+                                                    T *out, int32_t *status) {
+    constexpr int P = Geo<T>::P;
+    __shared__ int64_t s_items[1024], s_nodes[1024];
+    const int tid = threadIdx.x;
+    const int64_t per = (B + blockDim.x - 1) / blockDim.x;
+    const int64_t v0 = min(B, tid * per), v1 = min(B, v0 + per);
+    int kk = kitem; // work-item depth; deepened below if the tickets would not fit
+    auto plan_of = [&](int64_t v, VecPlan &pl, int64_t &items, int64_t &nodes, int32_t &st) {
+        const int64_t a = off[v];
+        const int64_t b = lens ? ((lens[v] >= 0 && a <= x_len - lens[v]) ? a + lens[v] : -1) : off[v + 1];
+        pl = VecPlan{};
+        items = 0;
+        nodes = 0;
+        st = NRM_OK;
+        if (a < 0 || b < a || b > x_len || (pdev && !plan_op<T>(pdev[v], pl))) {
+            st = NRM_EINVAL;
+            return;
+        }
+        const int64_t n = b - a;
+        pl.x_off = a;
+        pl.n = n;
+        pl.stride = 1;
+        if (n == 0) return;
+        pl.m = (n + P - 1) / P;
+        pl.D = ceil_log2_i64(pl.m);
+        int k = min(pl.D, kk);
+        if (pl.D - k > dwmax) k = pl.D - dwmax;
+        if (k > kmax) {
+            st = NRM_EINVAL; // larger than the tree kernel supports (> 2^33 rows)
+            return;
+        }
+        pl.k = k;
+        pl.dw = pl.D - k;
+        items = int64_t(1) << pl.dw;
+        nodes = items - 1;
+    };
+    int64_t si, sn;
+    for (;;) {
+        si = 0;
+        sn = 0;
+        for (int64_t v = v0; v < v1; ++v) {
+            VecPlan pl;
+            int64_t it, nd;
+            int32_t st;
+            plan_of(v, pl, it, nd, st);
+            si += it;
+            sn += nd;
+        }
+        s_items[tid] = si;
+        s_nodes[tid] = sn;
+        __syncthreads();
+        // Hillis-Steele inclusive scan over the 1024 partial sums
+        for (int d = 1; d < 1024; d <<= 1) {
+            int64_t ai = 0, an = 0;
+            if (tid >= d) {
+                ai = s_items[tid - d];
+                an = s_nodes[tid - d];
+            }
+            __syncthreads();
+            s_items[tid] += ai;
+            s_nodes[tid] += an;
+            __syncthreads();
+        }
+        // segments may overlap, so their nodes are not bounded by x_len:
+        // deeper work items need fewer tickets (the tree is unchanged)
+        if (s_nodes[blockDim.x - 1] <= node_cap || kk >= kmax) break;
+        __syncthreads();
+        ++kk;
+    }
+    // If even the deepest work items need more ticket nodes than the
+    // workspace holds, no vector is computed and all report NRM_ENOMEM.
+    const bool overflow = s_nodes[blockDim.x - 1] > node_cap;
+    const int64_t total_items = s_items[blockDim.x - 1], total_nodes = s_nodes[blockDim.x - 1];
+    const int64_t nb0 = s_nodes[tid] - sn; // this thread's first ticket node (vector order)
+    const int64_t ib0 = s_items[tid] - si; // its first work item in vector order
+    // statuses and the outputs of empty or bad vectors
+    for (int64_t v = v0; v < v1; ++v) {
+        VecPlan pl;
+        int64_t it, nd;
+        int32_t st;
+        plan_of(v, pl, it, nd, st);
+        if (overflow && st == NRM_OK) st = NRM_ENOMEM;
+        if (status) status[v] = st;
+        if (st != NRM_OK) out[v] = T(NAN);
+        else if (pl.n == 0) out[v] = T(0);
+    }
+    // Work order: the persistent grid takes work items in index order, so
+    // the vectors are numbered longest first (a counting sort on n in
+    // quarter-octave classes, the last bucket for vectors without work
+    // items) and the
+    // plans stored in that order, their item bases increasing with the index,
+    // each with its vector's output index.  Within a bucket the order comes
+    // from one 64-bit atomic per vector that returns its slot (high 20 bits)
+    // and its first item (low 44 bits) together, so it may differ between
+    // calls: it decides which warp computes a subtree, never the tree.
+    // Ticket nodes keep the vector order.
+    // classes of a quarter octave: floor(log2 n) and the next two bits of n
+    constexpr int NB = 4 * 41 + 1;
+    __shared__ unsigned long long s_cnt[NB];
+    __shared__ int64_t s_vbase[NB], s_ibase[NB];
+    const bool sorted = B < (int64_t(1) << 20) && total_items < (int64_t(1) << 44);
+    auto bucket_of = [&](int64_t n, int64_t items) {
+        if (items == 0 || overflow) return NB - 1;
+        const int lg = 63 - __clzll((long long)n); // n >= 1
+        const int cls = lg >= 40 ? 4 * 40 + 3 : 4 * lg + (lg >= 2 ? (int)((n >> (lg - 2)) & 3) : 0);
+        return NB - 2 - cls;
+    };
+    __syncthreads(); // every reader of the scans above is done
+    for (int q = tid; q < NB; q += blockDim.x) s_cnt[q] = 0ull;
+    __syncthreads();
+    if (sorted) {
+        for (int64_t v = v0; v < v1; ++v) {
+            VecPlan pl;
+            int64_t it, nd;
+            int32_t st;
+            plan_of(v, pl, it, nd, st);
+            atomicAdd(&s_cnt[bucket_of(pl.n, it)], (1ull << 44) | (unsigned long long)(overflow ? 0 : it));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int64_t vb = 0, ibs = 0;
+        for (int q = 0; q < NB; ++q) {
+            s_vbase[q] = vb;
+            s_ibase[q] = ibs;
+            vb += (int64_t)(s_cnt[q] >> 44);
+            ibs += (int64_t)(s_cnt[q] & ((1ull << 44) - 1));
+            s_cnt[q] = 0ull;
+        }
+    }
+    __syncthreads();
+    int64_t nbr = nb0, ib_unsorted = ib0;
+    for (int64_t v = v0; v < v1; ++v) {
+        VecPlan pl;
+        int64_t it, nd;
+        int32_t st;
+        plan_of(v, pl, it, nd, st);
+        if (overflow) it = 0;
+        pl.node_base = nbr;
+        pl.out_idx = v;
+        if (sorted) {
+            const int q = bucket_of(pl.n, it);
+            const unsigned long long got = atomicAdd(&s_cnt[q], (1ull << 44) | (unsigned long long)it);
+            pl.item_base = s_ibase[q] + (int64_t)(got & ((1ull << 44) - 1));
+            plans[s_vbase[q] + (int64_t)(got >> 44)] = pl;
+        } else {
+            pl.item_base = ib_unsorted;
+            plans[v] = pl;
+            ib_unsorted += it;
+        }
+        nbr += nd;
+    }
+    if (tid == blockDim.x - 1) {
+        totals[0] = overflow ? 0 : total_items;
+        totals[1] = total_nodes;
+        *cursor = 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+constexpr int DW_MAX = 20;
+
+template <typename T> constexpr int P_of() { return Geo<T>::P; }
+
+// Workspace layout of one call (the tickets live in their own buffer, see
+// nrm_ctx::tickets, so that no other data ever occupies a ticket).
+struct Layout {
+    size_t slots, plans, totals, cursor, end;
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+static Layout layout_for(int64_t nodes, int64_t B) {
+    Layout L;
+    L.slots = 0;
+    L.plans = align256(512 * (size_t)std::max<int64_t>(2 * nodes, 1));
+    L.totals = L.plans + align256(sizeof(VecPlan) * (size_t)std::max<int64_t>(B, 1));
+    L.cursor = L.totals + 256;
+    L.end = L.cursor + 256;
+    return L;
+}
+
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static nrm_status set_cuda_err(nrm_ctx *c, cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return NRM_OK;
+    if (c) {
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    if (e == cudaErrorMemoryAllocation) return NRM_ENOMEM;
+    return NRM_ECUDA;
+}
+
+// single-vector planning ------------------------------------------------------
+
+// Plan of one vector of n elements with P lanes: cut depth dw so that there
+// are enough work items to fill the GPU (at least min_items when the tree is
+// deep enough) but items no smaller than 2^G rows and no more than 2^DW_MAX.
+static bool plan_single(const nrm_ctx *c, int64_t n, int P, VecPlan &pl) {
+    const nrm_tuning &tu = c->tune[P == 64 ? NRM_F64 : NRM_F32];
+    pl = VecPlan{};
+    pl.n = n;
+    pl.stride = 1;
+    pl.m = (n + P - 1) / P;
+    pl.D = ceil_log2_i64(pl.m);
+    const int G = tu.group_log2;
+    const int64_t min_items = (int64_t)c->sms * tu.warps_per_block * 2;
+    int dw_fill = ceil_log2_i64(min_items);
+    int dw = std::max(pl.D - tu.item_log2, dw_fill);
+    dw = std::min(dw, pl.D - G);
+    dw = std::max(dw, 0);
+    dw = std::min(dw, DW_MAX);
+    int k = pl.D - dw;
+    if (k > G + MAXL) return false;
+    pl.k = k;
+    pl.dw = dw;
+    return true;
+}
+
+template <typename T> static const nrm_tuning &tune_of(const nrm_ctx *c) {
+    return c->tune[sizeof(T) == 8 ? NRM_F64 : NRM_F32];
+}
+
+template <typename T, class Op, bool FinalA = false>
+static cudaError_t launch_tree(nrm_ctx *c, const TreeArgs<T> &a, const Op &op, int64_t grid_warps,
+                               cudaStream_t s) {
+    const nrm_tuning &tu = tune_of<T>(c);
+    const int wpb = tu.warps_per_block;
+    int occ = 0;
+    int64_t blocks = 0;
+    cudaError_t e = cudaSuccess;
+    switch (tu.group_log2) {
+#define NRM_LAUNCH_G(GG)                                                                                    \
+    case GG: {                                                                                              \
+        const size_t smem = tree_smem_bytes<GG, Op>(wpb, a.levels);                                        \
+        cudaFuncSetAttribute(tree_kernel<T, GG, Op, FinalA>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                             (int)smem);                                                                    \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<T, GG, Op, FinalA>, wpb * 32, smem); \
+        occ = std::max(1, std::min(occ, tu.blocks_per_sm));                                                \
+        blocks = std::max<int64_t>(1, std::min<int64_t>((grid_warps + wpb - 1) / wpb, (int64_t)c->sms * occ)); \
+        tree_kernel<T, GG, Op, FinalA><<<(unsigned)blocks, wpb * 32, smem, s>>>(a, op);                     \
+        e = cudaGetLastError();                                                                             \
+        break;                                                                                              \
+    }
+        NRM_LAUNCH_G(2)
+        NRM_LAUNCH_G(3)
+#undef NRM_LAUNCH_G
+    default: return cudaErrorInvalidValue;
+    }
+    c->launches++;
+    return e;
+}
+
+// p -> combine op dispatch (Section 4): 2 -> v1_hypot, 1 -> sumabs,
+// inf -> maxabs, other -> v1_lp with p/2 and 1/p rounded once in T.  From
+// the cut-off p' on (Section 4) pow(Z, 1/p) is 1 for every Z in [1, 2], so
+// v1_lp returns max(|x|, |y|): p >= 2^53 (binary64) / 2^24 (binary32) takes
+// the maxabs code, which gives the same bits.
+template <typename T, class F> static cudaError_t with_op(T p, F &&f) {
+    const T cut = sizeof(T) == 8 ? T(9007199254740992.0) : T(16777216.0f);
+    if (p == T(2)) return f(OpHypot<T>{});
+    if (p == T(1)) return f(OpSumAbs<T>{});
+    if (p >= cut) return f(OpMaxAbs<T>{});
+    OpLp<T> o;
+    o.h = p * T(0.5);
+    o.ip = T(1) / p;
+    return f(o);
+}
+
+template <typename T>
+static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cudaStream_t s, int64_t item_lo,
+                             int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1, int variant = 0) {
+    VecPlan pl;
+    if (plan_in) pl = *plan_in;
+    else if (!plan_single(c, n, P_of<T>(), pl)) return NRM_EINVAL;
+    if (!plan_in) pl.stride = stride;
+    const int64_t items = int64_t(1) << pl.dw;
+    const int64_t nodes = items - 1;
+    Layout L = layout_for(nodes, 1);
+    nrm_status st = nrm_ctx_ensure(c, L.end, nodes);
+    if (st != NRM_OK) return st;
+    TreeArgs<T> a{};
+    a.x = x;
+    a.out = out;
+    a.plans = nullptr;
+    a.one = pl;
+    a.B = 1;
+    a.item_lo = plan_in ? item_lo : 0;
+    a.item_hi = plan_in ? item_hi : items;
+    a.total_items = nullptr;
+    a.cursor = nullptr;
+    a.tickets = c->tickets;
+    a.slots = reinterpret_cast<T *>((char *)c->ws + L.slots);
+    a.levels = stack_levels(pl.k, tune_of<T>(c).group_log2);
+    const int64_t warps = a.item_hi - a.item_lo;
+    cudaError_t e;
+    // variant 0: the combine of p; 1: Z with A (cr_hypot for the lane
+    // reduction); 2: the exponent-scaled hypotenuse K2 throughout
+    if (variant == 1) e = launch_tree<T, OpHypot<T>, true>(c, a, OpHypot<T>{}, warps, s);
+    else if (variant == 2) e = launch_tree<T, OpHypot2<T>>(c, a, OpHypot2<T>{}, warps, s);
+    else e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, warps, s); });
+    return set_cuda_err(c, e, "tree_kernel launch");
+}
+
+// (for segments that may overlap, the plan kernel's overflow guard applies)
+static int64_t batch_nodes_bound(const nrm_ctx *c, int64_t x_len, int64_t B, int P) {
+    // sum over vectors of 2^dw - 1 < 2 (m_v / 2^k) summed, m_v <= n_v/P + 1
+    const int k = c->tune[P == 64 ? NRM_F64 : NRM_F32].item_log2;
+    const int64_t rows = x_len / P + B + 1;
+    return (2 * rows >> k) + 2;
+}
+
+// The batch kernel with one p per vector, launched from nrm_tree_mixed.cu.
+cudaError_t launch_mixed(nrm_ctx *c, const TreeArgs<double> &a, int64_t grid_warps, cudaStream_t s);
+cudaError_t launch_mixed(nrm_ctx *c, const TreeArgs<float> &a, int64_t grid_warps, cudaStream_t s);
+
+template <typename T>
+static cudaError_t launch_tree_mixed(nrm_ctx *c, const TreeArgs<T> &a, int64_t grid_warps, cudaStream_t s) {
+    const nrm_tuning &tu = tune_of<T>(c);
+    const int wpb = tu.warps_per_block;
+    int occ = 0;
+    int64_t blocks = 0;
+    cudaError_t e = cudaSuccess;
+    switch (tu.group_log2) {
+#define NRM_LAUNCH_MIXED(GG)                                                                                \
+    case GG: {                                                                                              \
+        const size_t smem = tree_smem_bytes<GG, OpHypot<T>>(wpb, a.levels); /* the largest of the ops */   \
+        cudaFuncSetAttribute(tree_kernel_mixed<T, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel_mixed<T, GG>, wpb * 32, smem);      \
+        occ = std::max(1, std::min(occ, tu.blocks_per_sm));                                                \
+        blocks = std::max<int64_t>(1, std::min<int64_t>((grid_warps + wpb - 1) / wpb, (int64_t)c->sms * occ)); \
+        tree_kernel_mixed<T, GG><<<(unsigned)blocks, wpb * 32, smem, s>>>(a);                               \
+        e = cudaGetLastError();                                                                             \
+        break;                                                                                              \
+    }
+        NRM_LAUNCH_MIXED(2)
+        NRM_LAUNCH_MIXED(3)
+#undef NRM_LAUNCH_MIXED
+    default: return cudaErrorInvalidValue;
+    }
+    c->launches++;
+    return e;
+}
+
+template <typename T>
+static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t *off, const int64_t *lens,
+                            int64_t B, T p, const double *p_dev, T *out, int32_t *status, cudaStream_t s) {
+    constexpr int P = Geo<T>::P;
+    const int64_t nodes_bound = batch_nodes_bound(c, x_len, B, P);
+    Layout L = layout_for(nodes_bound, B);
+    nrm_status st = nrm_ctx_ensure(c, L.end, nodes_bound);
+    if (st != NRM_OK) return st;
+    char *ws = (char *)c->ws;
+    VecPlan *plans = reinterpret_cast<VecPlan *>(ws + L.plans);
+    int64_t *totals = reinterpret_cast<int64_t *>(ws + L.totals);
+    unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + L.cursor);
+    const nrm_tuning &tu = tune_of<T>(c);
+    // Deepest work item: vectors of offsets never overlap, so the ticket
+    // bound holds at item_log2 and a vector's k is at most item_log2 or
+    // D - DW_MAX for the longest possible vector (x_len elements); the plan
+    // kernel reports NRM_EINVAL for any vector deeper than kmax.  Segments
+    // may overlap and deepen their items, up to G + MAXL.
+    int kmax = tu.group_log2 + MAXL;
+    if (!lens) {
+        const int dmax = ceil_log2_i64(std::max<int64_t>(1, (x_len + P - 1) / P));
+        kmax = std::min(kmax, std::max(std::min(dmax, tu.item_log2), dmax - DW_MAX));
+        kmax = std::max(kmax, tu.group_log2);
+    }
+    plan_kernel<T><<<1, 1024, 0, s>>>(off, lens, p_dev, B, x_len, tu.item_log2, DW_MAX, kmax, nodes_bound, plans,
+                                      totals, cursor, out, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_err(c, e, "plan_kernel launch");
+    TreeArgs<T> a{};
+    a.x = x;
+    a.out = out;
+    a.plans = plans;
+    a.B = B;
+    a.total_items = totals;
+    a.cursor = cursor;
+    a.tickets = c->tickets;
+    a.slots = reinterpret_cast<T *>(ws + L.slots);
+    a.levels = stack_levels(kmax, tu.group_log2);
+    const int64_t persistent = (int64_t)c->sms * 64 * tu.warps_per_block; // capped by occupancy
+    if (p_dev) e = launch_mixed(c, a, persistent, s);
+    else e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, persistent, s); });
+    return set_cuda_err(c, e, "tree_kernel launch (batch)");
+}
+
+// The single-vector and batch entry points of each element type (defined in
+// nrm_tree_d.cu and nrm_tree_s.cu).
+nrm_status run_single_x(nrm_ctx *c, const double *x, int64_t n, double p, double *out, cudaStream_t s,
+                        int64_t item_lo, int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1,
+                        int variant = 0);
+nrm_status run_single_x(nrm_ctx *c, const float *x, int64_t n, float p, float *out, cudaStream_t s, int64_t item_lo,
+                        int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1, int variant = 0);
+nrm_status run_batch_x(nrm_ctx *c, const double *x, int64_t x_len, const int64_t *off, const int64_t *lens,
+                       int64_t B, double p, const double *p_dev, double *out, int32_t *status, cudaStream_t s);
+nrm_status run_batch_x(nrm_ctx *c, const float *x, int64_t x_len, const int64_t *off, const int64_t *lens,
+                       int64_t B, float p, const double *p_dev, float *out, int32_t *status, cudaStream_t s);
+
+} // namespace nrm

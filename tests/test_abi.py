@@ -38,7 +38,7 @@ def test_null_context_is_einval(L):
     assert L.nrmf_d(None, vp(0), 10, vp(0), None) == nrm.NRM_EINVAL
     assert L.nrmf_s(None, vp(0), 10, vp(0), None) == nrm.NRM_EINVAL
     assert L.nrmp_d(None, vp(0), 10, 3.0, vp(0), None) == nrm.NRM_EINVAL
-    assert L.nrm_batch(None, 1, vp(0), 0, vp(0), 1, 2.0, vp(0), vp(0), None) == nrm.NRM_EINVAL
+    assert L.nrm_batch(None, 1, vp(0), 0, vp(0), 1, 2.0, None, vp(0), vp(0), None) == nrm.NRM_EINVAL
     assert L.nrm_host(None, 1, vp(0), 1, 2.0, vp(0)) == nrm.NRM_EINVAL
     assert L.nrm_destroy(None) == nrm.NRM_OK
 

@@ -235,7 +235,7 @@ def test_invalid_arguments(nrm):
     assert L.nrmp_d(c.h, vp(x.data_ptr()), 5, 0.0, vp(o.data_ptr()), None) == nrm.NRM_EINVAL
     assert L.nrmp_d(c.h, vp(x.data_ptr()), 5, -2.0, vp(o.data_ptr()), None) == nrm.NRM_EINVAL
     assert L.nrmp_d(c.h, vp(x.data_ptr()), 5, float("nan"), vp(o.data_ptr()), None) == nrm.NRM_EINVAL
-    assert L.nrm_batch(c.h, 5, vp(x.data_ptr()), 8, vp(0), 1, 2.0, vp(o.data_ptr()), vp(0), None) == nrm.NRM_EINVAL
+    assert L.nrm_batch(c.h, 5, vp(x.data_ptr()), 8, vp(0), 1, 2.0, None, vp(o.data_ptr()), vp(0), None) == nrm.NRM_EINVAL
     # n == 0 gives +0
     o.fill_(7.0)
     assert L.nrmf_d(c.h, vp(0), 0, vp(o.data_ptr()), None) == nrm.NRM_OK

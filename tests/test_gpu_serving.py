@@ -63,6 +63,9 @@ def test_server_results_equal_alone(nrm):
         norms, lat, rep = srv.replay(tr)
         assert rep["completed"] == len(tr) and rep["rejected"] == 0
         assert rep["steps"] < len(tr)  # requests were batched
+        # one segment batch per element type and step (a p per request):
+        # at most 2 groups x (plan + tree launch)
+        assert rep["launches"] <= 4 * rep["steps"]
         assert 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
         for i in range(len(tr)):
             r = tr[i]

@@ -911,3 +911,19 @@ def test_nrm_es_against_binary128(dt):
     v = float(oracle.nrm_es(np.full(n, c, dt)))
     bound = (1 + 1.75 * eps * (1 + 2.0 ** -20)) ** oracle.tree_depth(n, P) - 1
     assert abs(v - 1.7 * math.sqrt(n)) <= bound * 1.7 * math.sqrt(n) + 1.7 * math.sqrt(n) * eps
+
+
+def test_thread_driver_is_bitwise_the_serial_tree():
+    """The oracle's all-cores driver (the top splits of Listing 4's recursion
+    evaluated on separate threads) gives the serial oracle's bits for every
+    thread count, length and combine."""
+    r = random.Random(77)
+    for trial in range(24):
+        n = r.choice([1, 2, 63, 64, 65, 129, 1000, 12345, 1 << 16, (1 << 18) + 7, r.randint(1, 400000)])
+        dt = np.float64 if trial % 2 == 0 else np.float32
+        p = r.choice([2.0, 1.0, 3.0, 1.5, math.inf])
+        x = inputs.vector(n, seed=trial, vec=1, dtype=dt)
+        want = oracle.nrm(x, p)
+        for t in (1, 2, 3, 8, 16):
+            got = oracle.nrm_par(x, p, threads=t)
+            assert got.tobytes() == want.tobytes(), (n, dt, p, t)
