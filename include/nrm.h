@@ -244,6 +244,49 @@ nrm_status nrm_graph_launch(nrm_graph *graph, void *stream);
 nrm_status nrm_graph_destroy(nrm_graph *graph);
 
 /*
+ * Sharding one vector across 2^dg devices (Section 2, Eq. hr: the norms of
+ * disjoint parts combine by one more hypot; Section 3.1 reduces per-column
+ * norms the same way).  The vector's row tree (see the top of this file) is
+ * cut at depth dg: device j holds the elements of node j, computes that
+ * node's P lane partials (one 512-byte row) with nrm_node_lanes, the 2^dg
+ * rows are gathered (512 bytes per device, e.g. one all-gather), and
+ * nrm_combine_nodes combines them through the tree's top dg levels and
+ * reduces the lanes: the result is bitwise the one-device nrmp_* result.
+ *
+ * nrm_shard_range (host only, no device work): node j of depth dg of the
+ * tree over n elements of `dtype` holds elements [*first, *first + *count)
+ * (count 0 when the node has no rows, i.e. n is below 2^dg rows' worth).
+ * NRM_EINVAL for a bad dtype, n < 0, dg outside [0, NRM_SHARD_MAX_DEPTH],
+ * j outside [0, 2^dg) or NULL outputs.
+ */
+#define NRM_SHARD_MAX_DEPTH 16
+nrm_status nrm_shard_range(nrm_dtype dtype, int64_t n, int32_t dg, int64_t j, int64_t *first, int64_t *count);
+
+/*
+ * The P lane partials of one node: Z of Listing 4 over the node's `count`
+ * elements x[0..count) (device pointer, any element alignment) with the
+ * combine of p (as nrmp_*), without the final lane reduction; lanes: device
+ * pointer to P elements of `dtype` (512 bytes), written asynchronously
+ * (zeros when count == 0).  Uses the context's workspace.  Errors as
+ * nrmp_*, plus NRM_EINVAL for lanes == NULL.
+ */
+nrm_status nrm_node_lanes(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t count, double p, void *lanes,
+                          void *stream);
+
+/*
+ * Combine the 2^dg node rows lanes[j P .. j P + P) (device, in node order j;
+ * overwritten: the buffer holds intermediate rows afterwards) of a vector of
+ * n elements through the top dg levels of its row tree -- the left node is
+ * the left operand, a node without rows passes its sibling through -- and
+ * reduce the root's P lanes by R (Listing 1, contiguous pairing): *out (one
+ * device element) = ||x||_p, bitwise equal to nrmp_* on the whole vector.
+ * Errors: NRM_EINVAL for NULL pointers, n < 0, dg outside
+ * [0, NRM_SHARD_MAX_DEPTH], a bad dtype, p <= 0 or NaN.
+ */
+nrm_status nrm_combine_nodes(nrm_ctx *ctx, nrm_dtype dtype, void *lanes, int32_t dg, int64_t n, double p, void *out,
+                             void *stream);
+
+/*
  * End-to-end call on HOST buffers: copies x_host[0..n) to the device in
  * chunks that overlap with the tree computation, computes ||x||_p as
  * nrmp_*, and copies the result to *out_host; returns when it is there.

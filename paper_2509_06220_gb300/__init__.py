@@ -120,6 +120,9 @@ def load():
         "nrm_test_inject_alloc_failures": (None, [ctypes.c_int]),
         "nrm_test_read_tickets": (st, [vp, vp, i64]),
         "nrm_probe_pipe": (st, [i32, i64, i32, vp, ctypes.POINTER(i64), vp]),
+        "nrm_shard_range": (st, [i32, i64, i32, i64, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "nrm_node_lanes": (st, [vp, i32, vp, i64, ctypes.c_double, vp, vp]),
+        "nrm_combine_nodes": (st, [vp, i32, vp, i32, i64, ctypes.c_double, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         if hasattr(L, name):
@@ -592,6 +595,64 @@ def nrm_matrix(buf, M, N, lda, p=2.0, out=None, stream=None, ctx=None):
                           ctypes.c_void_p(out.data_ptr()), _stream(stream))
     c.check(r, "nrm_matrix")
     return out
+
+
+def shard_range(n, dg, j, dtype=NRM_F64):
+    """(first, count): the elements of node j at depth dg of the row tree of
+    a vector of n elements -- the part device j of 2^dg holds."""
+    first, count = ctypes.c_int64(), ctypes.c_int64()
+    r = load().nrm_shard_range(int(dtype), int(n), int(dg), int(j), ctypes.byref(first), ctypes.byref(count))
+    if r != NRM_OK:
+        raise NrmError(r, "nrm_shard_range")
+    return first.value, count.value
+
+
+def node_lanes(x, p=2.0, out=None, stream=None, ctx=None):
+    """The P lane partials (one 512-byte row) of a node held as the 1-D CUDA
+    tensor x (its elements in order)."""
+    import torch
+    _check_vec(x)
+    dt = _dtype_code(x)
+    c = ctx or context(x.device)
+    if out is None:
+        out = torch.empty(P_LANES[dt], dtype=x.dtype, device=x.device)
+    c.check(load().nrm_node_lanes(c.h, dt, ctypes.c_void_p(x.data_ptr() if x.numel() else 0), x.numel(), float(p),
+                                  ctypes.c_void_p(out.data_ptr()), _stream(stream)), "nrm_node_lanes")
+    return out
+
+
+def combine_nodes(lanes, dg, n, p=2.0, out=None, stream=None, ctx=None):
+    """||x||_p from the 2^dg node rows of x (a CUDA tensor of 2^dg x P
+    elements in node order; overwritten) for a vector of n elements."""
+    import torch
+    dt = _dtype_code(lanes)
+    if not lanes.is_cuda or not lanes.is_contiguous() or lanes.numel() != (1 << dg) * P_LANES[dt]:
+        raise ValueError("lanes must be a contiguous CUDA tensor of 2^dg x P elements")
+    c = ctx or context(lanes.device)
+    if out is None:
+        out = torch.empty((), dtype=lanes.dtype, device=lanes.device)
+    c.check(load().nrm_combine_nodes(c.h, dt, ctypes.c_void_p(lanes.data_ptr()), int(dg), int(n), float(p),
+                                     ctypes.c_void_p(out.data_ptr()), _stream(stream)), "nrm_combine_nodes")
+    return out
+
+
+def nrm_sharded(x_local, n, p=2.0, group=None, ctx=None):
+    """||x||_p of a vector of n elements sharded over the 2^dg ranks of a
+    torch.distributed group (rank j holds shard_range(n, dg, j)'s elements
+    as the CUDA tensor x_local): each rank computes its node's lanes, the
+    512-byte rows are all-gathered (through host memory, so any backend
+    works), and every rank combines them; bitwise the one-device result."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    dg = world.bit_length() - 1
+    if world != 1 << dg:
+        raise ValueError("the group size must be a power of two")
+    mine = node_lanes(x_local, p, ctx=ctx).cpu()
+    rows = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(rows, mine, group=group)
+    lanes = torch.cat(rows).to(x_local.device)
+    return combine_nodes(lanes, dg, n, p, ctx=ctx)
 
 
 PIPE_DFMA, PIPE_DMUL, PIPE_FFMA = 0, 1, 2

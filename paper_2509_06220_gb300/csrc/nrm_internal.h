@@ -29,6 +29,7 @@ struct nrm_ctx {
     int64_t tickets_cap = 0;
     void *aux = nullptr; // matrix norms: column starts, lengths and norms
     size_t aux_bytes = 0;
+    void *node_args = nullptr; // nrm_node_lanes: the one-vector offsets, p and output (256 bytes)
     nrm_tuning tune[2]{}; // per element type: [NRM_F32], [NRM_F64]
     std::string err;
     uint64_t launches = 0;

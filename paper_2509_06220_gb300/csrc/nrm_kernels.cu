@@ -109,6 +109,7 @@ extern "C" nrm_status nrm_destroy(nrm_ctx *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->tickets) cudaFree(ctx->tickets);
     if (ctx->aux) cudaFree(ctx->aux);
+    if (ctx->node_args) cudaFree(ctx->node_args);
     delete ctx;
     return NRM_OK;
 }
@@ -352,6 +353,137 @@ nrm_status nrm_batch_impl(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t 
     const float pf = p_dev ? 2.0f : (float)p;
     if (!(pf > 0.0f)) return NRM_EINVAL;
     return run_batch_x(ctx, (const float *)x, x_len, offsets, lens, B, pf, p_dev, (float *)out, status, s);
+}
+
+// sharding across devices (Section 2, Eq. hr) ----------------------------------
+//
+// Norms of disjoint parts combine by one more combine, so a vector split at
+// the nodes of depth dg of its canonical row tree (rank j holds node j's
+// rows) gives, node by node, the lane partials of those subtrees; combining
+// the 2^dg lane vectors through the tree's top dg levels and reducing the
+// lanes reproduces the one-device result bit for bit.
+
+extern "C" nrm_status nrm_shard_range(nrm_dtype dtype, int64_t n, int32_t dg, int64_t j, int64_t *first,
+                                      int64_t *count) {
+    if ((dtype != NRM_F32 && dtype != NRM_F64) || n < 0 || dg < 0 || dg > NRM_SHARD_MAX_DEPTH || j < 0 ||
+        j >= (int64_t(1) << dg) || !first || !count)
+        return NRM_EINVAL;
+    const int64_t P = dtype == NRM_F64 ? 64 : 128;
+    const int64_t m = (n + P - 1) / P;
+    // node j at depth dg of the ceil-split tree over m rows: rows
+    // ceil((m - brev_dg(j)) / 2^dg) (zero when brev_dg(j) >= m), first row
+    // from the walk down from the root (left child: ceil of half the rows)
+    uint32_t b = 0;
+    for (int l = 0; l < dg; ++l) b |= (uint32_t)((j >> l) & 1) << (dg - 1 - l);
+    const int64_t rows = (int64_t)b >= m ? 0 : ((m - (int64_t)b) + (int64_t(1) << dg) - 1) >> dg;
+    int64_t start = 0, size = m;
+    for (int l = dg - 1; l >= 0; --l) {
+        const int64_t left = (size + 1) >> 1;
+        if ((j >> l) & 1) {
+            start += left;
+            size -= left;
+        } else {
+            size = left;
+        }
+    }
+    *first = std::min(start * P, n);
+    *count = rows == 0 ? 0 : std::min(rows * P, n - start * P);
+    return NRM_OK;
+}
+
+namespace {
+__global__ void node_args_kernel(int64_t *off, double *pd, int64_t n, double p) {
+    off[0] = 0;
+    off[1] = n;
+    pd[0] = p;
+}
+
+// One warp: node (d - 1, i) = combine(node (d, 2i), node (d, 2i + 1)) for
+// d = dg .. 1, in place (pair i overwrites slot i after reading 2i and
+// 2i + 1, in increasing i, so nothing is read after it was overwritten); a
+// node without rows passes its sibling through.  Each thread touches only its
+// own V lanes of every node, so no synchronisation is needed.  Then R over
+// the lanes of the root.
+template <typename T, class Op>
+__global__ void combine_nodes_kernel(T *lanes, int dg, int64_t m, Op op, T *out) {
+    constexpr int V = Geo<T>::V;
+    constexpr int P = Geo<T>::P;
+    const int lane = threadIdx.x & 31;
+    for (int d = dg; d >= 1; --d) {
+        for (uint32_t i = 0; i < (1u << (d - 1)); ++i) {
+            const bool a = node_rows(m, 2 * i, d) > 0, b = node_rows(m, 2 * i + 1, d) > 0;
+            T *dst = lanes + (size_t)i * P + lane * V;
+            const T *l = lanes + (size_t)(2 * i) * P + lane * V;
+            const T *r = lanes + (size_t)(2 * i + 1) * P + lane * V;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const T x = l[j], y = r[j];
+                dst[j] = (a && b) ? op(x, y) : (a ? x : y);
+            }
+        }
+    }
+    T r[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) r[j] = lanes[lane * V + j];
+    const T res = lane_reduce<T, Op>(r, op, lane);
+    if (lane == 0) *out = res;
+}
+} // namespace
+
+extern "C" nrm_status nrm_node_lanes(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t count, double p,
+                                     void *lanes, void *stream) {
+    if (!ctx || !lanes || count < 0 || (count > 0 && !x) || (dtype != NRM_F32 && dtype != NRM_F64) || !(p > 0.0) ||
+        (dtype == NRM_F32 && !((float)p > 0.0f)))
+        return NRM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = dtype == NRM_F64 ? 8 : 4;
+    if (count == 0) return set_cuda_err(ctx, cudaMemsetAsync(lanes, 0, 512, s), "cudaMemsetAsync(lanes)");
+    if (!ctx->node_args) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return set_cuda_err(ctx, e, "cudaStreamSynchronize");
+        if (nrm_test_fail_alloc()) return NRM_ENOMEM;
+        e = cudaMalloc(&ctx->node_args, 256);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->node_args = nullptr;
+            return set_cuda_err(ctx, e, "cudaMalloc(node_args)");
+        }
+    }
+    int64_t *off = (int64_t *)ctx->node_args;
+    double *pd = (double *)((char *)ctx->node_args + 64);
+    void *one = (char *)ctx->node_args + 128;
+    node_args_kernel<<<1, 1, 0, s>>>(off, pd, count, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_cuda_err(ctx, e, "node_args_kernel");
+    (void)es;
+    if (dtype == NRM_F64)
+        return run_batch_x(ctx, (const double *)x, count, off, nullptr, 1, 2.0, pd, (double *)one, nullptr, s,
+                           (double *)lanes);
+    return run_batch_x(ctx, (const float *)x, count, off, nullptr, 1, 2.0f, pd, (float *)one, nullptr, s,
+                       (float *)lanes);
+}
+
+extern "C" nrm_status nrm_combine_nodes(nrm_ctx *ctx, nrm_dtype dtype, void *lanes, int32_t dg, int64_t n, double p,
+                                        void *out, void *stream) {
+    if (!ctx || !lanes || !out || n < 0 || dg < 0 || dg > NRM_SHARD_MAX_DEPTH ||
+        (dtype != NRM_F32 && dtype != NRM_F64) || !(p > 0.0) || (dtype == NRM_F32 && !((float)p > 0.0f)))
+        return NRM_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t P = dtype == NRM_F64 ? 64 : 128;
+    if (n == 0) return set_cuda_err(ctx, cudaMemsetAsync(out, 0, dtype == NRM_F64 ? 8 : 4, s), "cudaMemsetAsync");
+    const int64_t m = (n + P - 1) / P;
+    cudaError_t e;
+    if (dtype == NRM_F64)
+        e = with_op<double>(p, [&](auto op) {
+            combine_nodes_kernel<double><<<1, 32, 0, s>>>((double *)lanes, dg, m, op, (double *)out);
+            return cudaGetLastError();
+        });
+    else
+        e = with_op<float>((float)p, [&](auto op) {
+            combine_nodes_kernel<float><<<1, 32, 0, s>>>((float *)lanes, dg, m, op, (float *)out);
+            return cudaGetLastError();
+        });
+    return set_cuda_err(ctx, e, "combine_nodes_kernel");
 }
 
 extern "C" nrm_status nrm_batch_segments(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len,

@@ -59,6 +59,7 @@ template <typename T> struct TreeArgs {
     unsigned *tickets;
     T *slots;
     int levels;                    // counter-stack rows per warp: max k - G of the launch
+    T *lanes;                      // batch with a p per vector, B = 1: the root stores its P lane partials here
 };
 
 // R over the P lanes held by the warp (Listing 1 with contiguous pairing):
@@ -131,7 +132,9 @@ static int stack_levels(int kmax, int G) { return std::max(0, std::min(MAXL, kma
 // above the cut, and -- for whoever combines the root -- the lane reduction
 // and the store of the result.
 // stk: this warp's counter stack; ring: its cp.async ring (ops with stages).
-template <typename T, int G, class Op, bool FinalA>
+// MayStoreLanes: when a.lanes is set, the root's P lane partials are stored
+// there (a shard's node of the row tree) instead of being reduced.
+template <typename T, int G, class Op, bool FinalA, bool MayStoreLanes = false>
 __device__ __forceinline__ void process_item(const TreeArgs<T> &a, const VecPlan &pl, int64_t v, int64_t gi,
                                              int lane, bool batch, const Op &op, T *stk,
                                              typename Geo<T>::vec *ring) {
@@ -193,6 +196,12 @@ __device__ __forceinline__ void process_item(const TreeArgs<T> &a, const VecPlan
         h >>= 1;
     }
     if (root) {
+        if constexpr (MayStoreLanes) {
+            if (a.lanes) {
+                store_row<T>(a.lanes + lane * V, r);
+                return;
+            }
+        }
         T res;
         if constexpr (FinalA) res = lane_reduce<T, OpCrHypot<T>>(r, OpCrHypot<T>{}, lane);
         else res = lane_reduce<T, Op>(r, op, lane);
@@ -263,9 +272,11 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
 // A ragged batch with a p per vector: the same persistent loop, each work
 // item combined with its vector's op (a warp-uniform switch: an item belongs
 // to one vector), so every result is bitwise that of the single-p kernel for
-// that vector's p.  The register cap is the largest of the ops' caps (v1_lp).
+// that vector's p.  The register cap is v1_hypot's: the trees are latency-
+// bound and most of a serving mix is p = 2, while v1_lp loses little at that
+// cap (binary64 p = 3 at 2^26: 6.74 ms at 64 registers, 6.45 ms at 128).
 template <typename T, int G>
-__global__ void __maxnreg__(OpLp<T>::kMaxRegs) tree_kernel_mixed(TreeArgs<T> a) {
+__global__ void __maxnreg__(OpHypot<T>::kMaxRegs) tree_kernel_mixed(TreeArgs<T> a) {
     const int lane = threadIdx.x & 31;
     const int64_t total = *a.total_items;
     T *stk;
@@ -279,19 +290,21 @@ __global__ void __maxnreg__(OpLp<T>::kMaxRegs) tree_kernel_mixed(TreeArgs<T> a) 
         const VecPlan pl = a.plans[v];
         switch (pl.op) {
         case OP_HYPOT:
-            process_item<T, G, OpHypot<T>, false>(a, pl, v, gi, lane, true, OpHypot<T>{}, stk, ring);
+            process_item<T, G, OpHypot<T>, false, true>(a, pl, v, gi, lane, true, OpHypot<T>{}, stk, ring);
             break;
         case OP_LP: {
             OpLp<T> o;
             o.h = (T)pl.h;
             o.ip = (T)pl.ip;
-            process_item<T, G, OpLp<T>, false>(a, pl, v, gi, lane, true, o, stk, ring);
+            process_item<T, G, OpLp<T>, false, true>(a, pl, v, gi, lane, true, o, stk, ring);
             break;
         }
         case OP_SUMABS:
-            process_item<T, G, OpSumAbs<T>, false>(a, pl, v, gi, lane, true, OpSumAbs<T>{}, stk, ring);
+            process_item<T, G, OpSumAbs<T>, false, true>(a, pl, v, gi, lane, true, OpSumAbs<T>{}, stk, ring);
             break;
-        default: process_item<T, G, OpMaxAbs<T>, false>(a, pl, v, gi, lane, true, OpMaxAbs<T>{}, stk, ring); break;
+        default:
+            process_item<T, G, OpMaxAbs<T>, false, true>(a, pl, v, gi, lane, true, OpMaxAbs<T>{}, stk, ring);
+            break;
         }
         unsigned long long g1 = 0;
         if (lane == 0) g1 = atomicAdd(a.cursor, 1ull);
@@ -682,7 +695,8 @@ static cudaError_t launch_tree_mixed(nrm_ctx *c, const TreeArgs<T> &a, int64_t g
 
 template <typename T>
 static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t *off, const int64_t *lens,
-                            int64_t B, T p, const double *p_dev, T *out, int32_t *status, cudaStream_t s) {
+                            int64_t B, T p, const double *p_dev, T *out, int32_t *status, cudaStream_t s,
+                            T *lanes = nullptr) {
     constexpr int P = Geo<T>::P;
     const int64_t nodes_bound = batch_nodes_bound(c, x_len, B, P);
     Layout L = layout_for(nodes_bound, B);
@@ -718,6 +732,7 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
     a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>(ws + L.slots);
     a.levels = stack_levels(kmax, tu.group_log2);
+    a.lanes = lanes; // used by the p-per-vector kernel only (p_dev set, B = 1)
     const int64_t persistent = (int64_t)c->sms * 64 * tu.warps_per_block; // capped by occupancy
     if (p_dev) e = launch_mixed(c, a, persistent, s);
     else e = with_op<T>(p, [&](auto op) { return launch_tree<T>(c, a, op, persistent, s); });
@@ -731,9 +746,12 @@ nrm_status run_single_x(nrm_ctx *c, const double *x, int64_t n, double p, double
                         int variant = 0);
 nrm_status run_single_x(nrm_ctx *c, const float *x, int64_t n, float p, float *out, cudaStream_t s, int64_t item_lo,
                         int64_t item_hi, const VecPlan *plan_in, int64_t stride = 1, int variant = 0);
+// lanes (p_dev set, B = 1): store the vector's P lane partials there, no lane reduction
 nrm_status run_batch_x(nrm_ctx *c, const double *x, int64_t x_len, const int64_t *off, const int64_t *lens,
-                       int64_t B, double p, const double *p_dev, double *out, int32_t *status, cudaStream_t s);
+                       int64_t B, double p, const double *p_dev, double *out, int32_t *status, cudaStream_t s,
+                       double *lanes = nullptr);
 nrm_status run_batch_x(nrm_ctx *c, const float *x, int64_t x_len, const int64_t *off, const int64_t *lens,
-                       int64_t B, float p, const double *p_dev, float *out, int32_t *status, cudaStream_t s);
+                       int64_t B, float p, const double *p_dev, float *out, int32_t *status, cudaStream_t s,
+                       float *lanes = nullptr);
 
 } // namespace nrm

@@ -10,8 +10,9 @@ nrm_status run_single_x(nrm_ctx *c, const double *x, int64_t n, double p, double
 }
 
 nrm_status run_batch_x(nrm_ctx *c, const double *x, int64_t x_len, const int64_t *off, const int64_t *lens,
-                       int64_t B, double p, const double *p_dev, double *out, int32_t *status, cudaStream_t s) {
-    return run_batch<double>(c, x, x_len, off, lens, B, p, p_dev, out, status, s);
+                       int64_t B, double p, const double *p_dev, double *out, int32_t *status, cudaStream_t s,
+                       double *lanes) {
+    return run_batch<double>(c, x, x_len, off, lens, B, p, p_dev, out, status, s, lanes);
 }
 
 } // namespace nrm
