@@ -272,11 +272,16 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
 // A ragged batch with a p per vector: the same persistent loop, each work
 // item combined with its vector's op (a warp-uniform switch: an item belongs
 // to one vector), so every result is bitwise that of the single-p kernel for
-// that vector's p.  The register cap is v1_hypot's: the trees are latency-
-// bound and most of a serving mix is p = 2, while v1_lp loses little at that
-// cap (binary64 p = 3 at 2^26: 6.74 ms at 64 registers, 6.45 ms at 128).
+// that vector's p.  Register cap: binary64 takes v1_hypot's (64; most of a
+// serving mix is p = 2, and v1_lp loses nothing there: the config-2 batch
+// with p = 3 took 7.67 ms against 8.13 ms in the one-p kernel at 128);
+// binary32 takes v1_lp's (at v1_hypot's 72 the binary32 v1_lp spills:
+// 2.33 ms against 1.46 ms).
+template <typename T> struct MixedRegs {
+    static constexpr int value = sizeof(T) == 8 ? OpHypot<T>::kMaxRegs : OpLp<T>::kMaxRegs;
+};
 template <typename T, int G>
-__global__ void __maxnreg__(OpHypot<T>::kMaxRegs) tree_kernel_mixed(TreeArgs<T> a) {
+__global__ void __maxnreg__(MixedRegs<T>::value) tree_kernel_mixed(TreeArgs<T> a) {
     const int lane = threadIdx.x & 31;
     const int64_t total = *a.total_items;
     T *stk;
