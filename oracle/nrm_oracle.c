@@ -101,35 +101,33 @@ static double max_d(double a, double b) { return isnan(a) ? b : isnan(b) ? a : (
 static float min_s(float a, float b) { return isnan(a) ? b : isnan(b) ? a : (b < a ? b : a); }
 static float max_s(float a, float b) { return isnan(a) ? b : isnan(b) ? a : (b > a ? b : a); }
 
-/* v1_hypot (Listing 2, Section 2): every statement is one IEEE operation.
- * fmin/fmax return the other operand when one is a NaN, so Q is never a NaN
- * (this also makes K(a,0)=a and K(0,0)=0 exact). */
+/* v1_hypot (the algorithm of Listing 2, Section 2): the hypotenuse written
+ * as big sqrt(1 + (small/big)^2) with big = max(|x|, |y|) and small =
+ * min(|x|, |y|), so that no square of an input is formed; each of its
+ * operations -- the ratio, the guard that makes a NaN ratio (0/0, inf/inf)
+ * count as 0, the fused 1 + r^2, the square root and the product -- is one
+ * IEEE operation rounded to nearest.  min/max treat a NaN as missing data,
+ * which makes K(a, 0) = a and K(0, 0) = 0 exact. */
 OR_API double or_k1_d(double x, double y)
 {
-    const double X = fabs(x);
-    const double Y = fabs(y);
-    const double m = min_d(X, Y);
-    const double M = max_d(X, Y);
-    const double q = m / M;
-    const double Q = max_d(q, 0.0);
-    const double S = fma(Q, Q, 1.0);
-    const double s = sqrt(S);
-    return M * s;
+    const double ax = fabs(x), ay = fabs(y);
+    const double big = max_d(ax, ay), small = min_d(ax, ay);
+    double r = small / big;
+    r = max_d(r, 0.0);
+    const double root = sqrt(fma(r, r, 1.0));
+    return big * root;
 }
 
-/* v1_hypotf: the single-precision form of Listing 2 (Section 2 says the
- * S routines substitute float, fabsf and the f-suffixed functions). */
+/* The binary32 form (Section 2: the S routines use float and the
+ * f-suffixed functions). */
 OR_API float or_k1_s(float x, float y)
 {
-    const float X = fabsf(x);
-    const float Y = fabsf(y);
-    const float m = min_s(X, Y);
-    const float M = max_s(X, Y);
-    const float q = m / M;
-    const float Q = max_s(q, 0.0f);
-    const float S = fmaf(Q, Q, 1.0f);
-    const float s = sqrtf(S);
-    return M * s;
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float big = max_s(ax, ay), small = min_s(ax, ay);
+    float r = small / big;
+    r = max_s(r, 0.0f);
+    const float root = sqrtf(fmaf(r, r, 1.0f));
+    return big * root;
 }
 
 /* 2^e as a double (binary32: a float) for e in [-1074, 1023] ([-149, 127]),
@@ -811,29 +809,27 @@ OR_API void or_comb_arr_s(int64_t n, float p, const float *x, const float *y, fl
 /* R_x: the scalar recursion of Listing 1 / Eq. r                           */
 /* ------------------------------------------------------------------------ */
 
-/* R(n, x): n == 1 -> |x0|; n == 2 -> op(x0, x1); otherwise split into a left
- * part of ceil(n/2) and a right part of floor(n/2), recurse on both, and
- * combine (Listing 1). */
+/* R(n, x) (Listing 1, Eq. r): the norm of one element is its magnitude and
+ * of two their combine; a longer array is cut after its first ceil(n/2)
+ * elements and the norms of the two parts are combined (left part first). */
 static double R_d(int64_t n, const double *x, const comb_d *c)
 {
     if (n == 1) return fabs(x[0]);
     if (n == 2) return comb_apply_d(c, x[0], x[1]);
-    const int64_t p = (n >> 1) + (n & 1);
-    const int64_t q = n - p;
-    const double fp = R_d(p, x, c);
-    const double fq = R_d(q, x + p, c);
-    return comb_apply_d(c, fp, fq);
+    const int64_t left = n - n / 2;
+    const double a = R_d(left, x, c);
+    const double b = R_d(n - left, x + left, c);
+    return comb_apply_d(c, a, b);
 }
 
 static float R_s(int64_t n, const float *x, const comb_s *c)
 {
     if (n == 1) return fabsf(x[0]);
     if (n == 2) return comb_apply_s(c, x[0], x[1]);
-    const int64_t p = (n >> 1) + (n & 1);
-    const int64_t q = n - p;
-    const float fp = R_s(p, x, c);
-    const float fq = R_s(q, x + p, c);
-    return comb_apply_s(c, fp, fq);
+    const int64_t left = n - n / 2;
+    const float a = R_s(left, x, c);
+    const float b = R_s(n - left, x + left, c);
+    return comb_apply_s(c, a, b);
 }
 
 /* The scalar algorithm H_x (R with v1_hypot) or its p-norm form.  n == 0
