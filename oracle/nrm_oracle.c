@@ -386,46 +386,56 @@ static float pow2_s(int k)
 /*
  * or_pow_d(x, y) ~ x^y for x >= 0 and y > 0: the binary64 pow of Listing 5.
  * The paper leaves the pow to the platform (cr_pow, __builtin_pow, SLEEF);
- * this one is defined here in fixed-point integer arithmetic, with a
- * table-driven reduction in the manner of Tang's table-driven log and exp,
- * so that the oracle and the GPU compute the same bits and the pow needs no
- * FP64 operation.  A "Qk" integer v stands for v 2^-k; every right shift
+ * this one is defined here in fixed-point integer arithmetic, so that the
+ * oracle and the GPU compute the same bits and the pow needs no FP64
+ * operation.  x^y = 2^(y log2 x); log2 x is reduced by two multipliers with
+ * few bits (so that both products are exact in 64-bit integers), in the
+ * manner of table-driven logarithms with short reciprocals, and 2^t by a
+ * table of 2^(i/256).  A "Qk" integer v stands for v 2^-k; every right shift
  * of a magnitude is a floor.  Steps:
- *  1. x = M 2^(E-52), M in [2^52, 2^53).  j = the top 8 fraction bits of M;
- *     the reference significand is C_j = 2^52 + j 2^44 for j < 128 and
- *     2^52 + (j + 1) 2^44 for j >= 128 (then E += 1: f = M/2^53), so that
- *     x = 2^E F_j (1 + u) with F_j = C_j/2^52 or C_j/2^53 and
- *     u = (M - C_j)/C_j, |u| < 2^-8, u >= 0 below j = 128, u <= 0 above,
- *     and F_0 = F_255 = 1 (no cancellation next to x = 1).
- *  2. a = |u| = g/C_j with g = |M - C_j|: the normalised g (gn = g 2^lg)
- *     times R_j = RN(2^179/C_j) (128 bits), top 128 bits: a = Up 2^-(115+lg).
- *  3. log(1 + u) = a - a^2 Hp(a) (u >= 0) or -(a + a^2 Hm(a)) (u < 0) with
- *     Hp, Hm = sum_{i=0}^{7} (-+a)^i/(i+2) by Horner in Q63 (coefficients
- *     floor(2^63/(i+2)), a in Q71): the series of log(1+u) to u^9/9 (the
- *     first omitted term is below 2^-72 of it).  a^2 H from the top words
- *     (Uh^2 then times H), aligned to a's scale and added: L1m 2^-(115+lg).
- *  4. log2(1 + u) = L1m ILN2 (ILN2 = RN(2^127/ln 2), 128 bits; the three
- *     high partial products) = L2m 2^-(114+lg).
- *  5. log2 x = E + T_j + log2(1+u), T_j = RN(log2(F_j) 2^80): a Q116
- *     fixed-point sum, or, when E = 0 and T_j = 0 (x within 2^-8 of 1),
- *     the 128-bit L2m with its exponent (full relative precision).
+ *  1. x = M 2^(E-52), M in [2^52, 2^53); j = the top 8 fraction bits of M;
+ *     for j >= 128, E += 1 (x = 2^E M/2^53, M/2^53 in [3/4, 1)).
+ *  2. r1 = RN(2^17 / (256.5 + j)) (r1 = 512 for j = 0), an integer in
+ *     [256, 512]; U1 = M r1 - 2^61 exactly: 1 + u1 = M r1 / 2^61 with
+ *     |u1| <= 2^-8; log2 x = E + T1_j + log2(1 + u1), T1_j = log2(2^9/r1)
+ *     (j < 128) or log2(2^8/r1) (j >= 128), so T1_0 = T1_255 = 0 and x next
+ *     to 1 keeps its full relative precision.
+ *  3. j2 = round(u1 2^16) = (U1 + 2^44) >> 45 (|j2| <= 256) and
+ *     (1 + u1)(1 - j2 2^-16) = 1 + u2 exactly: U2 = (U1 - j2 2^45) 2^16 -
+ *     U1 j2 in Q77, |u2| < 2^-15.4; log2(1 + u1) = T2_j2 + log2(1 + u2),
+ *     T2_j2 = -log2(1 - j2 2^-16).
+ *  4. ln(1 + u) = u - u^2 C, C = 1/2 - u/3 + u^2/4 - u^3/5 (the series to
+ *     u^5/5; the first omitted term is below 2^-79 of u), with u = s a:
+ *     C2 = 1/4 -+ a/5 in Q31 from the top 32 bits of a, C1 = 1/3 -+ a C2 in
+ *     Q63 (a 32 x 32-bit product), C = 1/2 -+ a C1 in Q63, then a^2 C from
+ *     the top words (a normalised: a = an 2^-(77+lg)); |ln(1+u)| = a -+ a^2 C
+ *     as a 128-bit value with one bit of headroom (an 2^63 -+ a^2 C 2^(140+lg));
+ *     log2(1+u) = that times ILN2 = RN(2^127/ln 2) (the three high partial
+ *     products).  Every right shift here is a floor, and a shift by the word
+ *     size or more gives 0 (for a tiny u these terms vanish).
+ *  5. log2 x = E + T1_j + T2_j2 + log2(1+u2) in Q116 (T1 in Q88 and T2 in
+ *     Q96 from the tables), or, when E = 0, T1_j = 0 and j2 = 0 (x within
+ *     2^-17 of 1), the 128-bit log2(1+u2) with its exponent.
  *  6. t = y log2 x from y's 53-bit significand (192-bit product), truncated
  *     to Q64; |t| >= 2^11 overflows or underflows.
- *  7. k = floor(t), r = t - k = i/64 + rho (i = top 6 bits of r, rho <
- *     2^-6); v = rho ln 2 in Q70 (ln 2 = RN(2^64 ln 2)); e^v by its Taylor
- *     series to degree 7, Horner in Q63 (floor(2^63/k!)); 2^r = TE_i e^v
- *     with TE_i = RN(2^(i/64) 2^63) (a Q126 product).
- *  8. 2^k 2^r rounded to nearest (ties to even) to 53 bits, or to a
+ *  7. k = floor(t), t - k = i/256 + rho (rho < 2^-8); v = rho ln 2 in Q70
+ *     (ln 2 = RN(2^64 ln 2)); e^v by its Taylor series to degree 6 by Horner
+ *     (the v^6, v^5 and v^4 coefficients in Q32 from the top 32 bits of v,
+ *     the rest in Q63); 2^(t-k) = TE_i e^v with TE_i = RN(2^(i/256) 2^63)
+ *     (a Q126 product).
+ *  8. 2^k 2^(t-k) rounded to nearest (ties to even) to 53 bits, or to a
  *     multiple of 2^-1074 below 2^-1022; above 2^1024 it is +inf.
- * The tables: R_j by exact long division; T_j and TE_i from binary128 log2
- * and pow, rounded to nearest (pinned to the 400-bit values in the tests).
- * Exact cases: pow(0,y) = 0, pow(1,y) = 1, pow(inf,y) = inf, pow(x,0) = 1,
- * pow(x,inf) = 0 (x < 1) or inf (x > 1), and pow(2^a, b) = 2^(ab) whenever
- * ab is an integer (then u = 0, T_j = 0, r = 0 and TE_0 e^0 = 2^126).
+ * The tables: r1 from its integer definition; T1, T2 and TE from binary128
+ * log2 and pow, rounded to nearest (pinned to the 400-bit values in the
+ * tests).  Exact cases: pow(0,y) = 0, pow(1,y) = 1, pow(inf,y) = inf,
+ * pow(x,0) = 1, pow(x,inf) = 0 (x < 1) or inf (x > 1), and pow(2^a, b) =
+ * 2^(ab) whenever ab is an integer (then u1 = u2 = 0, T1 = T2 = 0, the
+ * fraction of t is 0 and TE_0 e^0 = 2^126).
  */
 #define PW_ILN2_HI 0xb8aa3b295c17f0bbull /* RN(2^127 / ln 2), high word */
 #define PW_ILN2_LO 0xbe87fed0691d3e89ull /* low word */
 #define PW_LN2 0xb17217f7d1cf79acull     /* RN(2^64 ln 2) */
+#define PW_J2MAX 256
 
 typedef __int128 i128;
 
@@ -440,49 +450,50 @@ static u128 u192_shr(u192 v, int s)
     return (v.lo >> s) | ((u128)v.hi << (128 - s));
 }
 
-static uint64_t pw_C(int j) { return (1ull << 52) + ((uint64_t)(j + (j >= 128 ? 1 : 0)) << 44); }
+/* r1_j = RN(2^18 / (513 + 2 j)), r1_0 = 512 */
+static uint32_t pw_r1(int j)
+{
+    if (j == 0) return 512;
+    const uint32_t den = 513u + 2u * (uint32_t)j, q = (1u << 18) / den, r = (1u << 18) % den;
+    return q + (2 * r >= den ? 1u : 0u);
+}
 
-static u128 PW_R[256];
-static i128 PW_T[256];
-static uint64_t PW_TE[64];
+static i128 PW_T1[256];            /* Q88 */
+static i128 PW_T2[2 * PW_J2MAX + 1]; /* Q96, index j2 + PW_J2MAX */
+static uint64_t PW_TE[256];        /* Q63 */
 static pthread_once_t pw_once = PTHREAD_ONCE_INIT;
+
+static i128 q_round(q128 v) { return (i128)Q_FLOOR(v + (q128)0.5); }
 
 static void pw_init(void)
 {
+    const q128 two88 = (q128)309485009821345068724781056.0;      /* 2^88 */
+    const q128 two96 = two88 * (q128)256.0;                      /* 2^96 */
     for (int j = 0; j < 256; ++j) {
-        const uint64_t C = pw_C(j);
-        /* R_j = RN(2^179 / C): restoring long division of 2^179 by C */
-        u128 q = 0;
-        uint64_t r = 0;
-        for (int b = 179; b >= 0; --b) {
-            r = 2 * r + (b == 179 ? 1 : 0);
-            q <<= 1;
-            if (r >= C) { r -= C; q |= 1; }
-        }
-        if (2 * r >= C) q += 1; /* no ties: C is not a power of two unless r = 0 */
-        PW_R[j] = q;
-        /* T_j = RN(log2(F_j) 2^80) */
-        const q128 F = (q128)C / (j >= 128 ? (q128)9007199254740992.0 : (q128)4503599627370496.0);
-        const q128 L = Q_LOG2(F) * (q128)1208925819614629174706176.0; /* 2^80 */
-        PW_T[j] = (i128)Q_FLOOR(L + (q128)0.5);
+        const q128 r1 = (q128)pw_r1(j);
+        PW_T1[j] = q_round(Q_LOG2((j < 128 ? (q128)512 : (q128)256) / r1) * two88);
     }
-    for (int i = 0; i < 64; ++i) {
-        const q128 v = Q_POW((q128)2, (q128)i / 64) * (q128)9223372036854775808.0; /* 2^63 */
-        PW_TE[i] = (uint64_t)Q_FLOOR(v + (q128)0.5);
-    }
+    for (int j2 = -PW_J2MAX; j2 <= PW_J2MAX; ++j2)
+        PW_T2[j2 + PW_J2MAX] = q_round(-Q_LOG2((q128)1 - (q128)j2 / (q128)65536) * two96);
+    for (int i = 0; i < 256; ++i)
+        PW_TE[i] = (uint64_t)q_round(Q_POW((q128)2, (q128)i / 256) * (q128)9223372036854775808.0); /* 2^63 */
 }
 
-/* the tables, for the tests (R as {hi, lo}, T as two's complement {hi, lo}) */
-OR_API void or_pow_tables_d(uint64_t *R, uint64_t *T, uint64_t *TE)
+/* the tables, for the tests (r1 as integers, T1 and T2 as two's complement
+ * {hi, lo} pairs) */
+OR_API void or_pow_tables_d(uint64_t *R1, uint64_t *T1, uint64_t *T2, uint64_t *TE)
 {
     pthread_once(&pw_once, pw_init);
     for (int j = 0; j < 256; ++j) {
-        R[2 * j] = (uint64_t)(PW_R[j] >> 64);
-        R[2 * j + 1] = (uint64_t)PW_R[j];
-        T[2 * j] = (uint64_t)((u128)PW_T[j] >> 64);
-        T[2 * j + 1] = (uint64_t)(u128)PW_T[j];
+        R1[j] = pw_r1(j);
+        T1[2 * j] = (uint64_t)((u128)PW_T1[j] >> 64);
+        T1[2 * j + 1] = (uint64_t)(u128)PW_T1[j];
+        TE[j] = PW_TE[j];
     }
-    for (int i = 0; i < 64; ++i) TE[i] = PW_TE[i];
+    for (int k = 0; k < 2 * PW_J2MAX + 1; ++k) {
+        T2[2 * k] = (uint64_t)((u128)PW_T2[k] >> 64);
+        T2[2 * k + 1] = (uint64_t)(u128)PW_T2[k];
+    }
 }
 
 /* RN(P / 2^s), ties to even, for 1 <= s < 128 */
@@ -493,6 +504,13 @@ static u128 rne_shr(u128 P, int s)
     if (rem > half || (rem == half && (q & 1))) q += 1;
     return q;
 }
+
+static uint64_t mulhi64(uint64_t a, uint64_t b) { return (uint64_t)(((u128)a * b) >> 64); }
+static uint32_t mulhi32(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
+/* floor(v / 2^s) for any s >= 0 (a shift by the word size or more gives 0,
+ * which C leaves undefined) */
+static uint32_t srl32(uint32_t v, int s) { return s >= 32 ? 0u : v >> s; }
+static uint64_t srl64(uint64_t v, int s) { return s >= 64 ? 0ull : v >> s; }
 
 OR_API double or_pow_d(double x, double y)
 {
@@ -509,44 +527,46 @@ OR_API double or_pow_d(double x, double y)
     decompose_d(x, &M, &E);
     E += 52;
     const int j = (int)((M >> 44) & 255);
-    const int up = j >= 128;
-    E += up;
-    const uint64_t C = pw_C(j);
-    const uint64_t g = up ? C - M : M - C;
-    /* steps 2-4: log2(1 + u) = (up ? -1 : 1) L2m 2^L2e */
+    if (j >= 128) E += 1;
+    /* step 2 */
+    const int64_t U1 = (int64_t)(M * (uint64_t)pw_r1(j) - (1ull << 61));
+    /* step 3 */
+    const int64_t j2 = (U1 + ((int64_t)1 << 44)) >> 45;
+    const int64_t U2 = (int64_t)((uint64_t)(U1 - j2 * ((int64_t)1 << 45)) << 16) - U1 * j2;
+    /* step 4: log2(1 + u2) = (s ? -1 : 1) L2m 2^-(139 + lg) */
+    const int s = U2 < 0;
     u128 L2m = 0;
     int lg = 0;
-    if (g != 0) {
-        lg = clz64(g);
-        const uint64_t gn = g << lg;
-        const u128 R = PW_R[j];
-        const u128 Up = (u128)gn * (uint64_t)(R >> 64) + (((u128)gn * (uint64_t)R) >> 64);
-        const uint64_t a71 = (uint64_t)(Up >> (44 + lg));
-        uint64_t H = (1ull << 63) / 9;
-        for (int i = 6; i >= 0; --i) {
-            const uint64_t t = (uint64_t)(((u128)H * a71) >> 64) >> 7;
-            const uint64_t c = (1ull << 63) / (uint64_t)(i + 2);
-            H = up ? c + t : c - t;
-        }
-        const uint64_t Uh = (uint64_t)(Up >> 64);
-        const uint64_t S2 = (uint64_t)(((u128)Uh * Uh) >> 64);
-        const uint64_t Wq = (uint64_t)(((u128)S2 * H) >> 64);
-        const u128 Wa = (u128)Wq << (78 - lg);
-        const u128 L1m = up ? Up + Wa : Up - Wa;
-        const uint64_t Lh = (uint64_t)(L1m >> 64), Ll = (uint64_t)L1m;
+    if (U2 != 0) {
+        const uint64_t aint = s ? (uint64_t)(-U2) : (uint64_t)U2;
+        lg = clz64(aint);
+        const uint64_t an = aint << lg;
+        const uint32_t ahi = (uint32_t)(an >> 32);
+        const uint32_t t5 = srl32(mulhi32(ahi, 0x33333333u), 14 + lg);           /* a/5 in Q31 */
+        const uint32_t C2 = s ? (1u << 29) + t5 : (1u << 29) - t5;                 /* Q31 */
+        const uint64_t t1 = srl64((uint64_t)ahi * C2, 13 + lg);                     /* a C2 in Q63 */
+        const uint64_t C1 = s ? 0x2aaaaaaaaaaaaaabull + t1 : 0x2aaaaaaaaaaaaaabull - t1; /* Q63 */
+        const uint64_t t0 = srl64(mulhi64(an, C1), 13 + lg);                        /* a C1 in Q63 */
+        const uint64_t C = s ? (1ull << 62) + t0 : (1ull << 62) - t0;               /* Q63 */
+        const uint64_t sq = mulhi64(an, an);                                        /* a^2 2^(90+2lg) */
+        const uint64_t m2 = mulhi64(sq, C);                                         /* a^2 C 2^(89+2lg) */
+        const u128 corr = lg <= 51 ? (u128)m2 << (51 - lg) : (u128)srl64(m2, lg - 51);
+        const u128 Ln = s ? ((u128)an << 63) + corr : ((u128)an << 63) - corr;     /* |ln(1+u)| 2^(140+lg) < 2^128 */
+        const uint64_t Lh = (uint64_t)(Ln >> 64), Ll = (uint64_t)Ln;
         L2m = (u128)Lh * PW_ILN2_HI + (((u128)Lh * PW_ILN2_LO) >> 64) + (((u128)Ll * PW_ILN2_HI) >> 64);
     }
     /* step 5: log2 x = (neg ? -1 : 1) Lm 2^eL */
     u128 Lm;
     int eL;
     int neg;
-    if (E == 0 && PW_T[j] == 0) {
+    if (E == 0 && PW_T1[j] == 0 && j2 == 0) {
         Lm = L2m;
-        eL = -(114 + lg);
-        neg = up;
+        eL = -(139 + lg);
+        neg = s;
     } else {
-        const u128 l2 = g != 0 ? L2m >> (lg - 2) : 0;
-        const i128 Lq = (i128)E * ((i128)1 << 116) + PW_T[j] * ((i128)1 << 36) + (up ? -(i128)l2 : (i128)l2);
+        const u128 l2 = U2 != 0 ? L2m >> (23 + lg) : 0;
+        const i128 Lq = (i128)E * ((i128)1 << 116) + PW_T1[j] * ((i128)1 << 28) +
+                        PW_T2[j2 + PW_J2MAX] * ((i128)1 << 20) + (s ? -(i128)l2 : (i128)l2);
         neg = Lq < 0;
         Lm = neg ? (u128)(-Lq) : (u128)Lq;
         eL = -116;
@@ -571,15 +591,18 @@ OR_API double or_pow_d(double x, double y)
     /* step 7 */
     const int k = (int)(tq >> 64);
     const uint64_t r = (uint64_t)tq;
-    const int i = (int)(r >> 58);
-    const uint64_t rho = r & ((1ull << 58) - 1);
+    const int i = (int)(r >> 56);
+    const uint64_t rho = r & ((1ull << 56) - 1);
     const uint64_t v70 = (uint64_t)(((u128)rho * PW_LN2) >> 58);
-    uint64_t fact = 5040; /* 7! */
-    uint64_t Ev = (1ull << 63) / fact;
-    for (int kk = 6; kk >= 0; --kk) {
-        fact = kk > 1 ? fact / (uint64_t)(kk + 1) : 1;
-        Ev = (1ull << 63) / fact + ((uint64_t)(((u128)Ev * v70) >> 64) >> 6);
-    }
+    const uint32_t v32 = (uint32_t)(v70 >> 38);                         /* v in Q32 */
+    uint32_t e32 = (uint32_t)((1ull << 32) / 720);
+    e32 = (uint32_t)((1ull << 32) / 120) + mulhi32(e32, v32);
+    e32 = (uint32_t)((1ull << 32) / 24) + mulhi32(e32, v32);          /* Q32 */
+    uint64_t Ev = (uint64_t)e32 << 31;                                  /* Q63 */
+    Ev = (1ull << 63) / 6 + (mulhi64(Ev, v70) >> 6);
+    Ev = (1ull << 62) + (mulhi64(Ev, v70) >> 6);
+    Ev = (1ull << 63) + (mulhi64(Ev, v70) >> 6);
+    Ev = (1ull << 63) + (mulhi64(Ev, v70) >> 6);
     const u128 P = (u128)PW_TE[i] * Ev; /* Q126 */
     /* step 8 */
     const int nb = (uint64_t)(P >> 64) ? 128 - clz64((uint64_t)(P >> 64)) : 64 - clz64((uint64_t)P);

@@ -1,17 +1,20 @@
 """Write nrm_pow_tables.h: the constants of the library's binary64 pow.
 
 The pow that v1_lp uses (Listing 5; Section 4 leaves the pow to the
-platform) is x^y = 2^(y log2 x) in fixed-point integer arithmetic with a
-table-driven reduction in the manner of Tang's table-driven log and exp.
-This script computes its tables with mpmath at 400 bits and rounds each
-entry to nearest:
+platform) is x^y = 2^(y log2 x) in fixed-point integer arithmetic; log2 x
+is reduced by two multipliers with few bits, so that both products are exact
+in 64-bit integers, in the manner of table-driven logarithms with short
+reciprocals, and 2^t by a table of 2^(i/256).  This script computes its
+tables with mpmath at 400 bits and rounds each entry to nearest:
 
-  C_j   = 2^52 + j 2^44 (j < 128), 2^52 + (j + 1) 2^44 (j >= 128), the
-          reference significand for the top 8 fraction bits j of x
-  R_j   = RN(2^179 / C_j), 128 bits, in [2^126, 2^127]
-  T_j   = RN(log2(F_j) 2^80), F_j = C_j 2^-52 (j < 128) or C_j 2^-53
-          (j >= 128); T_0 = T_255 = 0
-  TE_i  = RN(2^(i/64) 2^63), i = 0..63
+  r1_j  = RN(2^18 / (513 + 2 j)) for j = 1..255 and r1_0 = 512: the first
+          multiplier for the top 8 fraction bits j of x (M r1_j / 2^61 is
+          within 2^-8 of 1)
+  T1_j  = RN(log2(2^9 / r1_j) 2^88) (j < 128) or RN(log2(2^8 / r1_j) 2^88)
+          (j >= 128, where the exponent of x is taken one higher); T1_0 =
+          T1_255 = 0
+  T2_j2 = RN(-log2(1 - j2 2^-16) 2^96), j2 = -256..256 (index j2 + 256)
+  TE_i  = RN(2^(i/256) 2^63), i = 0..255
   ILN2  = RN(2^127 / ln 2), 128 bits
   LN2   = RN(2^64 ln 2)
 
@@ -24,28 +27,34 @@ import mpmath
 
 mpmath.mp.prec = 400
 HERE = os.path.dirname(os.path.abspath(__file__))
+J2MAX = 256
 
 
 def rn(v):
     return int(mpmath.floor(v + mpmath.mpf("0.5")))
 
 
-def c_of(j):
-    return (1 << 52) + ((j + (1 if j >= 128 else 0)) << 44)
+def r1_of(j):
+    if j == 0:
+        return 512
+    den = 513 + 2 * j
+    q, r = divmod(1 << 18, den)
+    return q + (1 if 2 * r >= den else 0)
 
 
 def tables():
     two = mpmath.mpf(2)
-    R = [rn(two ** 179 / c_of(j)) for j in range(256)]
-    T = [rn(mpmath.log(mpmath.mpf(c_of(j)) / two ** (53 if j >= 128 else 52), 2) * two ** 80) for j in range(256)]
-    TE = [rn(two ** (mpmath.mpf(i) / 64) * two ** 63) for i in range(64)]
+    R1 = [r1_of(j) for j in range(256)]
+    T1 = [rn(mpmath.log(mpmath.mpf(512 if j < 128 else 256) / R1[j], 2) * two ** 88) for j in range(256)]
+    T2 = [rn(-mpmath.log(1 - mpmath.mpf(j2) / 65536, 2) * two ** 96) for j2 in range(-J2MAX, J2MAX + 1)]
+    TE = [rn(two ** (mpmath.mpf(i) / 256) * two ** 63) for i in range(256)]
     ILN2 = rn(two ** 127 / mpmath.log(2))
     LN2 = rn(mpmath.log(2) * two ** 64)
-    return R, T, TE, ILN2, LN2
+    return R1, T1, T2, TE, ILN2, LN2
 
 
 def main():
-    R, T, TE, ILN2, LN2 = tables()
+    R1, T1, T2, TE, ILN2, LN2 = tables()
     M = (1 << 64) - 1
     out = []
     out.append("// nrm_pow_tables.h -- generated by gen_pow_tables.py; do not edit.")
@@ -54,21 +63,28 @@ def main():
     out.append("#pragma once")
     out.append("#include <cstdint>")
     out.append("namespace nrm {")
-    out.append("// R_j = RN(2^179 / C_j) as {high, low} words")
-    out.append("static __device__ const uint64_t kPowR[256][2] = {")
-    for j in range(0, 256, 2):
-        out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (R[k] >> 64, R[k] & M) for k in (j, j + 1)))
+    out.append("// r1_j, the first multiplier of the reduction")
+    out.append("static __device__ const uint16_t kPowR1[256] = {")
+    for j in range(0, 256, 16):
+        out.append("    " + " ".join("%d," % R1[k] for k in range(j, j + 16)))
     out.append("};")
-    out.append("// T_j = RN(log2(F_j) 2^80) as a two's-complement 128-bit {high, low}")
-    out.append("static __device__ const uint64_t kPowT[256][2] = {")
+    out.append("// T1_j = RN(log2(2^9 or 2^8 / r1_j) 2^88) as a two's-complement 128-bit {high, low}")
+    out.append("static __device__ const uint64_t kPowT1[256][2] = {")
     for j in range(0, 256, 2):
-        out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (((T[k] >> 64) & M), T[k] & M) for k in (j, j + 1)))
+        out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (((T1[k] >> 64) & M), T1[k] & M) for k in (j, j + 1)))
     out.append("};")
-    out.append("// TE_i = RN(2^(i/64) 2^63)")
-    out.append("static __device__ const uint64_t kPowTE[64] = {")
-    for i in range(0, 64, 4):
+    out.append("// T2_j2 = RN(-log2(1 - j2 2^-16) 2^96), index j2 + %d, as {high, low}" % J2MAX)
+    out.append("static __device__ const uint64_t kPowT2[%d][2] = {" % (2 * J2MAX + 1))
+    for k in range(0, 2 * J2MAX + 1, 2):
+        ks = [k] if k + 1 > 2 * J2MAX else [k, k + 1]
+        out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (((T2[i] >> 64) & M), T2[i] & M) for i in ks))
+    out.append("};")
+    out.append("// TE_i = RN(2^(i/256) 2^63)")
+    out.append("static __device__ const uint64_t kPowTE[256] = {")
+    for i in range(0, 256, 4):
         out.append("    " + " ".join("0x%016xull," % TE[k] for k in range(i, i + 4)))
     out.append("};")
+    out.append("constexpr int kPowJ2Max = %d;" % J2MAX)
     out.append("constexpr uint64_t kPowILN2_HI = 0x%016xull; // RN(2^127 / ln 2), high word" % (ILN2 >> 64))
     out.append("constexpr uint64_t kPowILN2_LO = 0x%016xull; // low word" % (ILN2 & M))
     out.append("constexpr uint64_t kPowLN2 = 0x%016xull;     // RN(2^64 ln 2)" % LN2)

@@ -455,17 +455,25 @@ def test_pow_constants_are_correctly_rounded():
 
 
 def _pow_table_definitions():
-    """The binary64 pow's tables from their definitions, at 400 bits:
-    C_j (the reference significand of the top 8 fraction bits j), R_j =
-    RN(2^179 / C_j), T_j = RN(log2(F_j) 2^80), TE_i = RN(2^(i/64) 2^63)."""
+    """The binary64 pow's tables from their definitions, at 400 bits: the
+    first multiplier r1_j = RN(2^18 / (513 + 2 j)) (512 for j = 0), T1_j =
+    RN(log2(2^9 / r1_j) 2^88) (j < 128) or RN(log2(2^8 / r1_j) 2^88),
+    T2_j2 = RN(-log2(1 - j2 2^-16) 2^96) for j2 = -256..256, TE_i =
+    RN(2^(i/256) 2^63)."""
+    from fractions import Fraction
     with mpmath.workprec(400):
         two = mpmath.mpf(2)
         rn = lambda v: int(mpmath.floor(v + mpmath.mpf("0.5")))
-        C = [(1 << 52) + ((j + (1 if j >= 128 else 0)) << 44) for j in range(256)]
-        R = [rn(two ** 179 / C[j]) for j in range(256)]
-        T = [rn(mpmath.log(mpmath.mpf(C[j]) / two ** (53 if j >= 128 else 52), 2) * two ** 80) for j in range(256)]
-        TE = [rn(two ** (mpmath.mpf(i) / 64) * two ** 63) for i in range(64)]
-    return C, R, T, TE
+        R1 = [512] + [int(Fraction(1 << 18, 513 + 2 * j) + Fraction(1, 2)) for j in range(1, 256)]
+        T1 = [rn(mpmath.log(mpmath.mpf(512 if j < 128 else 256) / R1[j], 2) * two ** 88) for j in range(256)]
+        T2 = [rn(-mpmath.log(1 - mpmath.mpf(k) / 65536, 2) * two ** 96) for k in range(-256, 257)]
+        TE = [rn(two ** (mpmath.mpf(i) / 256) * two ** 63) for i in range(256)]
+    return R1, T1, T2, TE
+
+
+def _s128(hi, lo):
+    v = int(hi) << 64 | int(lo)
+    return v - (1 << 128) if v >> 127 else v
 
 
 def _oracle_pow_tables():
@@ -473,23 +481,42 @@ def _oracle_pow_tables():
     L = oracle.lib()
     f = L.or_pow_tables_d
     f.restype = None
-    f.argtypes = [ctypes.c_void_p] * 3
-    Ro, To, TEo = np.zeros(512, np.uint64), np.zeros(512, np.uint64), np.zeros(64, np.uint64)
-    f(Ro.ctypes.data, To.ctypes.data, TEo.ctypes.data)
-    R = [int(Ro[2 * j]) << 64 | int(Ro[2 * j + 1]) for j in range(256)]
-    T = [(int(To[2 * j]) << 64 | int(To[2 * j + 1])) - ((1 << 128) if int(To[2 * j]) >> 63 else 0) for j in range(256)]
-    return R, T, [int(v) for v in TEo]
+    f.argtypes = [ctypes.c_void_p] * 4
+    R1, T1, T2, TE = np.zeros(256, np.uint64), np.zeros(512, np.uint64), np.zeros(2 * 513, np.uint64), \
+        np.zeros(256, np.uint64)
+    f(R1.ctypes.data, T1.ctypes.data, T2.ctypes.data, TE.ctypes.data)
+    return ([int(v) for v in R1], [_s128(T1[2 * j], T1[2 * j + 1]) for j in range(256)],
+            [_s128(T2[2 * k], T2[2 * k + 1]) for k in range(513)], [int(v) for v in TE])
 
 
 def test_pow_tables_match_their_definitions():
-    """The oracle builds the binary64 pow's tables itself (exact long
-    division for R_j, binary128 log2 and pow for T_j and TE_i); every entry
-    equals the 400-bit value rounded to nearest.  F_0 = F_255 = 1, so
-    T_0 = T_255 = 0: no cancellation next to x = 1."""
-    C, R, T, TE = _pow_table_definitions()
-    Ro, To, TEo = _oracle_pow_tables()
-    assert Ro == R and To == T and TEo == TE
-    assert T[0] == 0 and T[255] == 0 and R[0] == 1 << 127 and TE[0] == 1 << 63
+    """The oracle builds the binary64 pow's tables itself (binary128 log2
+    and pow); every entry equals the 400-bit value rounded to nearest.
+    T1_0 = T1_255 = 0 and T2_0 = 0: no cancellation next to x = 1."""
+    R1, T1, T2, TE = _pow_table_definitions()
+    assert _oracle_pow_tables() == (R1, T1, T2, TE)
+    assert T1[0] == 0 and T1[255] == 0 and T2[256] == 0 and R1[255] == 256 and TE[0] == 1 << 63
+
+
+def test_pow_reduction_bounds():
+    """The two short multipliers of the reduction, over every significand
+    bucket (its ends and random interior points): M r1_j is exact in 64
+    bits, |u1| <= 2^-8, |j2| <= 256 (the T2 table's range), and u2 is exact
+    in Q77 with |u2| < 2^-15.4 (the log series' range)."""
+    R1 = _pow_table_definitions()[0]
+    r = random.Random(12)
+    for j in range(256):
+        lo = (1 << 52) + (j << 44)
+        for M in [lo, lo + (1 << 44) - 1] + [r.randrange(lo, lo + (1 << 44)) for _ in range(200)]:
+            P1 = M * R1[j]
+            assert P1 < 1 << 62
+            U1 = P1 - (1 << 61)
+            assert abs(U1) <= 1 << 53
+            j2 = (U1 + (1 << 44)) >> 45
+            assert abs(j2) <= 256
+            U2 = ((U1 - j2 * (1 << 45)) << 16) - U1 * j2
+            assert U2 == (M * R1[j] * (65536 - j2) << 0) - (1 << 77)  # (1 + u1)(1 - j2 2^-16) - 1 exactly
+            assert abs(U2) < 2 ** 61.6
 
 
 def test_kernel_pow_tables_match_the_definitions():
@@ -502,18 +529,18 @@ def test_kernel_pow_tables_match_the_definitions():
                         "csrc", "nrm_pow_tables.h")
     src = open(path).read()
 
-    def block(name):
+    def block(name, pattern=r"0x([0-9a-f]+)ull", base=16):
         body = src[src.index(name):]
         body = body[body.index("{") + 1:body.index("};")]
-        return [int(v, 16) for v in re.findall(r"0x([0-9a-f]+)ull", body)]
+        return [int(v, base) for v in re.findall(pattern, body)]
 
-    C, R, T, TE = _pow_table_definitions()
-    r = block("kPowR[256][2]")
-    t = block("kPowT[256][2]")
-    te = block("kPowTE[64]")
-    assert [r[2 * j] << 64 | r[2 * j + 1] for j in range(256)] == R
-    assert [(t[2 * j] << 64 | t[2 * j + 1]) - ((1 << 128) if t[2 * j] >> 63 else 0) for j in range(256)] == T
-    assert te == TE
+    R1, T1, T2, TE = _pow_table_definitions()
+    assert block("kPowR1[256]", r"(\d+),", 10) == R1
+    t1 = block("kPowT1[256][2]")
+    t2 = block("kPowT2[513][2]")
+    assert [_s128(t1[2 * j], t1[2 * j + 1]) for j in range(256)] == T1
+    assert [_s128(t2[2 * k], t2[2 * k + 1]) for k in range(513)] == T2
+    assert block("kPowTE[256]") == TE
     with mpmath.workprec(400):
         iln2 = int(mpmath.floor(mpmath.mpf(2) ** 127 / mpmath.log(2) + mpmath.mpf("0.5")))
         ln2 = int(mpmath.floor(mpmath.log(2) * mpmath.mpf(2) ** 64 + mpmath.mpf("0.5")))
