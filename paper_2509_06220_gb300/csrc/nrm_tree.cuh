@@ -127,6 +127,13 @@ template <int G, class Op> constexpr size_t tree_smem_bytes(int wpb, int levels)
 // stack rows for work items of at most 2^kmax rows
 static int stack_levels(int kmax, int G) { return std::max(0, std::min(MAXL, kmax - G)); }
 
+// Ordering of the ticket tree: the warp that finishes a child stores its row,
+// then a device-scope acquire-release fence, then increments the parent's
+// ticket (relaxed); the second arriver reads the ticket, fences again and
+// loads its sibling's row -- fence-to-fence message passing, which needs no
+// sequentially consistent fence.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // One work item: global item gi, the item's subtree (index gi - item_base
 // at depth dw of vector v's row tree, plan pl), the climb of the ticket tree
 // above the cut, and -- for whoever combines the root -- the lane reduction
@@ -172,7 +179,7 @@ __device__ __forceinline__ void process_item(const TreeArgs<T> &a, const VecPlan
     while (h > 1) {
         T *mine = a.slots + ((size_t)(2 * pl.node_base + h - 2) * P) + lane * V;
         store_row<T>(mine, r);
-        __threadfence();
+        fence_acq_rel_gpu(); // release this row before the ticket
         __syncwarp();
         unsigned tk = 0;
         unsigned *ticket = a.tickets + (pl.node_base + (h >> 1) - 1);
@@ -183,7 +190,7 @@ __device__ __forceinline__ void process_item(const TreeArgs<T> &a, const VecPlan
             break;
         }
         if (lane == 0) atomicExch(ticket, 0u);
-        __threadfence();
+        fence_acq_rel_gpu(); // acquire the sibling's row after the ticket
         T sib[V];
         load_slot<T>(a.slots + ((size_t)(2 * pl.node_base + (h ^ 1u) - 2) * P) + lane * V, sib);
         if (h & 1u) {
@@ -425,82 +432,121 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     const int64_t total_items = s_items[blockDim.x - 1], total_nodes = s_nodes[blockDim.x - 1];
     const int64_t nb0 = s_nodes[tid] - sn; // this thread's first ticket node (vector order)
     const int64_t ib0 = s_items[tid] - si; // its first work item in vector order
-    // statuses and the outputs of empty or bad vectors
-    for (int64_t v = v0; v < v1; ++v) {
-        VecPlan pl;
-        int64_t it, nd;
-        int32_t st;
-        plan_of(v, pl, it, nd, st);
-        if (overflow && st == NRM_OK) st = NRM_ENOMEM;
-        if (status) status[v] = st;
-        if (st != NRM_OK) out[v] = T(NAN);
-        else if (pl.n == 0) out[v] = T(0);
-    }
     // Work order: the persistent grid takes work items in index order, so
-    // the vectors are numbered longest first (a counting sort on n in
-    // quarter-octave classes, the last bucket for vectors without work
-    // items) and the
-    // plans stored in that order, their item bases increasing with the index,
-    // each with its vector's output index.  Within a bucket the order comes
-    // from one 64-bit atomic per vector that returns its slot (high 20 bits)
-    // and its first item (low 44 bits) together, so it may differ between
-    // calls: it decides which warp computes a subtree, never the tree.
-    // Ticket nodes keep the vector order.
-    // classes of a quarter octave: floor(log2 n) and the next two bits of n
+    // the vectors are numbered longest first: a counting sort on n in
+    // quarter-octave classes (floor(log2 n) and its next two bits; the last
+    // class for vectors without work items), the plans stored in that order
+    // with their output index, and their item bases increasing with the
+    // plan index.  Within a class the order comes from warp-aggregated
+    // shared-memory atomics, so it may differ between calls: it decides which
+    // warp computes a subtree, never the tree.  Ticket nodes keep the vector
+    // order.  Every thread runs the same number of iterations (per), so the
+    // warp-wide match and shuffles see converged warps.
     constexpr int NB = 4 * 41 + 1;
-    __shared__ unsigned long long s_cnt[NB];
-    __shared__ int64_t s_vbase[NB], s_ibase[NB];
-    const bool sorted = B < (int64_t(1) << 20) && total_items < (int64_t(1) << 44);
+    __shared__ unsigned s_cnt[NB], s_cur[NB];
+    __shared__ int64_t s_vbase[256];
+    const bool sorted = B < (int64_t(1) << 31);
     auto bucket_of = [&](int64_t n, int64_t items) {
         if (items == 0 || overflow) return NB - 1;
         const int lg = 63 - __clzll((long long)n); // n >= 1
         const int cls = lg >= 40 ? 4 * 40 + 3 : 4 * lg + (lg >= 2 ? (int)((n >> (lg - 2)) & 3) : 0);
         return NB - 2 - cls;
     };
+    const int lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u; // lanes below this one
     __syncthreads(); // every reader of the scans above is done
-    for (int q = tid; q < NB; q += blockDim.x) s_cnt[q] = 0ull;
+    for (int q = tid; q < NB; q += blockDim.x) s_cnt[q] = s_cur[q] = 0u;
     __syncthreads();
-    if (sorted) {
-        for (int64_t v = v0; v < v1; ++v) {
+    // statuses, the outputs of empty or bad vectors, and the class counts
+    for (int64_t r = 0; r < per; ++r) {
+        const int64_t v = v0 + r;
+        const bool valid = v < v1;
+        int q = NB; // no class
+        if (valid) {
             VecPlan pl;
             int64_t it, nd;
             int32_t st;
             plan_of(v, pl, it, nd, st);
-            atomicAdd(&s_cnt[bucket_of(pl.n, it)], (1ull << 44) | (unsigned long long)(overflow ? 0 : it));
+            if (overflow && st == NRM_OK) st = NRM_ENOMEM;
+            if (status) status[v] = st;
+            if (st != NRM_OK) out[v] = T(NAN);
+            else if (pl.n == 0) out[v] = T(0);
+            q = bucket_of(pl.n, it);
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int64_t vb = 0, ibs = 0;
-        for (int q = 0; q < NB; ++q) {
-            s_vbase[q] = vb;
-            s_ibase[q] = ibs;
-            vb += (int64_t)(s_cnt[q] >> 44);
-            ibs += (int64_t)(s_cnt[q] & ((1ull << 44) - 1));
-            s_cnt[q] = 0ull;
-        }
-    }
-    __syncthreads();
-    int64_t nbr = nb0, ib_unsorted = ib0;
-    for (int64_t v = v0; v < v1; ++v) {
-        VecPlan pl;
-        int64_t it, nd;
-        int32_t st;
-        plan_of(v, pl, it, nd, st);
-        if (overflow) it = 0;
-        pl.node_base = nbr;
-        pl.out_idx = v;
         if (sorted) {
-            const int q = bucket_of(pl.n, it);
-            const unsigned long long got = atomicAdd(&s_cnt[q], (1ull << 44) | (unsigned long long)it);
-            pl.item_base = s_ibase[q] + (int64_t)(got & ((1ull << 44) - 1));
-            plans[s_vbase[q] + (int64_t)(got >> 44)] = pl;
-        } else {
+            const unsigned grp = __match_any_sync(FULL, q);
+            if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
+        }
+    }
+    __syncthreads();
+    // first plan index of every class: an exclusive scan over the classes
+    if (sorted) {
+        const int64_t c = tid < NB ? (int64_t)s_cnt[tid] : 0;
+        if (tid < 256) s_vbase[tid] = c;
+        __syncthreads();
+        for (int d = 1; d < 256; d <<= 1) {
+            const int64_t a = (tid < 256 && tid >= d) ? s_vbase[tid - d] : 0;
+            __syncthreads();
+            if (tid < 256) s_vbase[tid] += a;
+            __syncthreads();
+        }
+        if (tid < 256) s_vbase[tid] -= c;
+        __syncthreads();
+    }
+    // the plans: in class order (their item counts in item_base for now), or
+    // in vector order with their item bases
+    int64_t nbr = nb0, ib_unsorted = ib0;
+    for (int64_t r = 0; r < per; ++r) {
+        const int64_t v = v0 + r;
+        const bool valid = v < v1;
+        VecPlan pl;
+        int64_t it = 0, nd = 0;
+        int q = NB;
+        if (valid) {
+            int32_t st;
+            plan_of(v, pl, it, nd, st);
+            if (overflow) it = 0;
+            pl.node_base = nbr;
+            pl.out_idx = v;
+            nbr += nd;
+            q = bucket_of(pl.n, it);
+        }
+        if (sorted) {
+            const unsigned grp = __match_any_sync(FULL, q);
+            const int leader = __ffs(grp) - 1;
+            unsigned base = 0u;
+            if (valid && lane == leader) base = atomicAdd(&s_cur[q], (unsigned)__popc(grp));
+            base = __shfl_sync(FULL, base, leader);
+            if (valid) {
+                pl.item_base = it;
+                plans[s_vbase[q] + base + __popc(grp & lt)] = pl;
+            }
+        } else if (valid) {
             pl.item_base = ib_unsorted;
             plans[v] = pl;
             ib_unsorted += it;
         }
-        nbr += nd;
+    }
+    if (sorted) {
+        // item bases in plan order: a block scan over the plans' item counts
+        __syncthreads(); // the plans are written (visible within the block)
+        int64_t cnt = 0;
+        for (int64_t s = v0; s < v1; ++s) cnt += plans[s].item_base;
+        __syncthreads();
+        s_items[tid] = cnt;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {
+            const int64_t a = tid >= d ? s_items[tid - d] : 0;
+            __syncthreads();
+            s_items[tid] += a;
+            __syncthreads();
+        }
+        int64_t ib = s_items[tid] - cnt;
+        for (int64_t s = v0; s < v1; ++s) {
+            const int64_t c = plans[s].item_base;
+            plans[s].item_base = ib;
+            ib += c;
+        }
     }
     if (tid == blockDim.x - 1) {
         totals[0] = overflow ? 0 : total_items;
@@ -563,6 +609,9 @@ static bool plan_single(const nrm_ctx *c, int64_t n, int P, VecPlan &pl) {
     const int64_t min_items = (int64_t)c->sms * tu.warps_per_block * 2;
     int dw_fill = ceil_log2_i64(min_items);
     int dw = std::max(pl.D - tu.item_log2, dw_fill);
+    // a short vector: items of at least 2^(G+2) rows (filling the GPU with
+    // items of one group made the ticket tree above them the critical path)
+    dw = std::min(dw, std::max(pl.D - G - 2, 0));
     dw = std::min(dw, pl.D - G);
     dw = std::max(dw, 0);
     dw = std::min(dw, DW_MAX);
