@@ -49,8 +49,9 @@ nrm_status nrm_run_single_range(nrm_ctx *c, nrm_dtype dt, const void *x, int64_t
 nrm_status nrm_batch_impl(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,
                           int64_t B, double p, const double *p_dev, void *out, int32_t *status, cudaStream_t s,
                           const int64_t *lens = nullptr);
-size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);
-int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B);
+// workspace and ticket counters of a batch (per_vector_p: a p per vector)
+size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B, bool per_vector_p = false);
+int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B, bool per_vector_p = false);
 void nrm_graph_free(nrm_graph *g);
 void nrm_host_free(nrm_ctx *c);
 bool nrm_test_fail_alloc();

@@ -319,13 +319,13 @@ extern "C" nrm_status nrm_matrix(nrm_ctx *ctx, nrm_dtype dtype, const void *A, i
 // batch -----------------------------------------------------------------------
 
 
-int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B) {
-    return batch_nodes_bound(c, x_len, B, dt == NRM_F64 ? 64 : 128);
+int64_t nrm_batch_tickets(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B, bool per_vector_p) {
+    return batch_nodes_bound(c, x_len, B, dt == NRM_F64 ? 64 : 128, per_vector_p);
 }
 
-size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B) {
+size_t nrm_batch_ws_bytes(const nrm_ctx *c, nrm_dtype dt, int64_t x_len, int64_t B, bool per_vector_p) {
     const int P = dt == NRM_F64 ? 64 : 128;
-    return layout_for(batch_nodes_bound(c, x_len, B, P), B).end;
+    return layout_for(batch_nodes_bound(c, x_len, B, P, per_vector_p), B).end;
 }
 
 extern "C" size_t nrm_workspace_bytes(const nrm_ctx *ctx, nrm_dtype dtype, int64_t x_len, int64_t B) {

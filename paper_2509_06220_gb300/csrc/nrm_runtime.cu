@@ -44,7 +44,8 @@ extern "C" nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void 
     if (B <= 0 || !offsets || !out || x_len < 0 || (x_len > 0 && !x) || (!p_dev && !(p > 0.0)) ||
         (dtype != NRM_F32 && dtype != NRM_F64))
         return NRM_EINVAL;
-    nrm_status st = nrm_ctx_ensure(ctx, nrm_batch_ws_bytes(ctx, dtype, x_len, B), nrm_batch_tickets(ctx, dtype, x_len, B));
+    nrm_status st = nrm_ctx_ensure(ctx, nrm_batch_ws_bytes(ctx, dtype, x_len, B, p_dev != nullptr),
+                                   nrm_batch_tickets(ctx, dtype, x_len, B, p_dev != nullptr));
     if (st != NRM_OK) return st;
     cudaStream_t s;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -247,7 +248,7 @@ extern "C" nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t 
     };
     for (int G = 2; G <= 3 && st == NRM_OK; ++G)
         for (int wpb : {4, 8, 16})
-            for (int k = G + 3; k <= G + 6 && st == NRM_OK; ++k)
+            for (int k = G + 2; k <= G + 7 && st == NRM_OK; ++k)
                 for (int bps : {2, 4, 8, 16}) {
                     ctx->tune[dtype] = nrm_tuning{G, wpb, k, bps};
                     if (total == 0) break;

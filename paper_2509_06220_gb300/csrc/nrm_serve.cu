@@ -345,10 +345,10 @@ extern "C" nrm_status nrm_srv_create(nrm_srv **srv, int device, size_t budget_by
         // reserve the largest workspace a step can need: every element of
         // the arena in one batch of the narrowest type (most rows)
         const int64_t max_elems = (int64_t)(budget_bytes / 4);
-        const size_t ws = std::max(nrm_batch_ws_bytes(ln.ctx, NRM_F32, max_elems, max_batch),
-                                   nrm_batch_ws_bytes(ln.ctx, NRM_F64, max_elems / 2, max_batch));
-        const int64_t tk = std::max(nrm_batch_tickets(ln.ctx, NRM_F32, max_elems, max_batch),
-                                    nrm_batch_tickets(ln.ctx, NRM_F64, max_elems / 2, max_batch));
+        const size_t ws = std::max(nrm_batch_ws_bytes(ln.ctx, NRM_F32, max_elems, max_batch, true),
+                                   nrm_batch_ws_bytes(ln.ctx, NRM_F64, max_elems / 2, max_batch, true));
+        const int64_t tk = std::max(nrm_batch_tickets(ln.ctx, NRM_F32, max_elems, max_batch, true),
+                                    nrm_batch_tickets(ln.ctx, NRM_F64, max_elems / 2, max_batch, true));
         st = nrm_ctx_ensure(ln.ctx, ws, tk);
         if (st != NRM_OK) break;
         reserved += ws + (size_t)tk * 4;

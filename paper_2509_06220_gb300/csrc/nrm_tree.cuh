@@ -51,6 +51,7 @@ template <typename T> struct TreeArgs {
     const T *x;
     T *out;
     const VecPlan *plans; // batch: device plans; nullptr: single vector `one`
+    const int64_t *bases; // batch: the plans' item bases, compact (the owner search reads these)
     VecPlan one;
     int64_t B;
     int64_t item_lo, item_hi;      // single vector: item range of this launch
@@ -217,11 +218,13 @@ __device__ __forceinline__ void process_item(const TreeArgs<T> &a, const VecPlan
 }
 
 // the plan of the vector owning global item gi (last v with item_base <= gi)
+// (a binary search over the compact item bases, read through the read-only
+// cache: 8 bytes a plan instead of one 88-byte plan per step)
 template <typename T> __device__ __forceinline__ int64_t owner_of(const TreeArgs<T> &a, int64_t gi) {
     int64_t lo = 0, hi = a.B;
     while (hi - lo > 1) {
         const int64_t mid = (lo + hi) >> 1;
-        if (a.plans[mid].item_base <= gi) lo = mid;
+        if (__ldg(a.bases + mid) <= gi) lo = mid;
         else hi = mid;
     }
     return lo;
@@ -352,11 +355,14 @@ template <typename T> __device__ __forceinline__ bool plan_op(double pd, VecPlan
     return true;
 }
 
+constexpr int LP_FINER = 2;
+
 template <typename T>
 __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ off, const int64_t *__restrict__ lens,
                                                     const double *__restrict__ pdev, int64_t B, int64_t x_len,
                                                     int kitem, int dwmax, int kmax, int64_t node_cap,
-                                                    VecPlan *plans, int64_t *totals, unsigned long long *cursor,
+                                                    VecPlan *plans, int64_t *bases, int64_t *totals,
+                                                    unsigned long long *cursor,
                                                     T *out, int32_t *status) {
     constexpr int P = Geo<T>::P;
     __shared__ int64_t s_items[1024], s_nodes[1024];
@@ -382,7 +388,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         if (n == 0) return;
         pl.m = (n + P - 1) / P;
         pl.D = ceil_log2_i64(pl.m);
-        int k = min(pl.D, kk);
+        // with a p per vector, v1_lp vectors take items LP_FINER levels
+        // smaller: their combine is many times costlier, so a batch of them
+        // is otherwise one wave of long items at the kernel's register cap
+        int k = min(pl.D, (pdev && pl.op == OP_LP) ? max(kk - LP_FINER, 0) : kk);
         if (pl.D - k > dwmax) k = pl.D - dwmax;
         if (k > kmax) {
             st = NRM_EINVAL; // larger than the tree kernel supports (> 2^33 rows)
@@ -437,20 +446,28 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     // quarter-octave classes (floor(log2 n) and its next two bits; the last
     // class for vectors without work items), the plans stored in that order
     // with their output index, and their item bases increasing with the
-    // plan index.  Within a class the order comes from warp-aggregated
-    // shared-memory atomics, so it may differ between calls: it decides which
-    // warp computes a subtree, never the tree.  Ticket nodes keep the vector
-    // order.  Every thread runs the same number of iterations (per), so the
-    // warp-wide match and shuffles see converged warps.
-    constexpr int NB = 4 * 41 + 1;
+    // plan index.  With a p per vector the classes are ordered by combine
+    // first (v1_lp, v1_hypot, maxabs, sumabs: the costliest first), so that
+    // the warps of an SM mostly run one combine's code at a time (interleaved
+    // combines thrashed the instruction cache: 6.65 ms against 3.5 ms for the
+    // same batch split by p).  Within a class the order comes from
+    // warp-aggregated shared-memory atomics, so it may differ between calls:
+    // it decides which warp computes a subtree, never the tree.  Ticket nodes
+    // keep the vector order.  Every thread runs the same number of
+    // iterations (per), so the warp-wide match and shuffles see converged
+    // warps.
+    constexpr int NL = 4 * 41 + 1;   // length classes
+    constexpr int NB = 4 * NL;       // (combine, length) classes
     __shared__ unsigned s_cnt[NB], s_cur[NB];
-    __shared__ int64_t s_vbase[256];
+    __shared__ int64_t s_vbase[1024];
     const bool sorted = B < (int64_t(1) << 31);
-    auto bucket_of = [&](int64_t n, int64_t items) {
+    auto bucket_of = [&](const VecPlan &pl, int64_t items) {
         if (items == 0 || overflow) return NB - 1;
+        const int64_t n = pl.n;
         const int lg = 63 - __clzll((long long)n); // n >= 1
         const int cls = lg >= 40 ? 4 * 40 + 3 : 4 * lg + (lg >= 2 ? (int)((n >> (lg - 2)) & 3) : 0);
-        return NB - 2 - cls;
+        const int rank = !pdev ? 0 : pl.op == OP_LP ? 0 : pl.op == OP_HYPOT ? 1 : pl.op == OP_MAXABS ? 2 : 3;
+        return rank * NL + (NL - 2 - cls);
     };
     const int lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u; // lanes below this one
@@ -471,7 +488,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
             if (status) status[v] = st;
             if (st != NRM_OK) out[v] = T(NAN);
             else if (pl.n == 0) out[v] = T(0);
-            q = bucket_of(pl.n, it);
+            q = bucket_of(pl, it);
         }
         if (sorted) {
             const unsigned grp = __match_any_sync(FULL, q);
@@ -482,15 +499,15 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     // first plan index of every class: an exclusive scan over the classes
     if (sorted) {
         const int64_t c = tid < NB ? (int64_t)s_cnt[tid] : 0;
-        if (tid < 256) s_vbase[tid] = c;
+        s_vbase[tid] = c;
         __syncthreads();
-        for (int d = 1; d < 256; d <<= 1) {
-            const int64_t a = (tid < 256 && tid >= d) ? s_vbase[tid - d] : 0;
+        for (int d = 1; d < 1024; d <<= 1) {
+            const int64_t a = tid >= d ? s_vbase[tid - d] : 0;
             __syncthreads();
-            if (tid < 256) s_vbase[tid] += a;
+            s_vbase[tid] += a;
             __syncthreads();
         }
-        if (tid < 256) s_vbase[tid] -= c;
+        s_vbase[tid] -= c;
         __syncthreads();
     }
     // the plans: in class order (their item counts in item_base for now), or
@@ -509,7 +526,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
             pl.node_base = nbr;
             pl.out_idx = v;
             nbr += nd;
-            q = bucket_of(pl.n, it);
+            q = bucket_of(pl, it);
         }
         if (sorted) {
             const unsigned grp = __match_any_sync(FULL, q);
@@ -524,6 +541,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         } else if (valid) {
             pl.item_base = ib_unsorted;
             plans[v] = pl;
+            bases[v] = ib_unsorted;
             ib_unsorted += it;
         }
     }
@@ -545,6 +563,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         for (int64_t s = v0; s < v1; ++s) {
             const int64_t c = plans[s].item_base;
             plans[s].item_base = ib;
+            bases[s] = ib;
             ib += c;
         }
     }
@@ -565,7 +584,7 @@ template <typename T> constexpr int P_of() { return Geo<T>::P; }
 // Workspace layout of one call (the tickets live in their own buffer, see
 // nrm_ctx::tickets, so that no other data ever occupies a ticket).
 struct Layout {
-    size_t slots, plans, totals, cursor, end;
+    size_t slots, plans, bases, totals, cursor, end;
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -574,7 +593,8 @@ static Layout layout_for(int64_t nodes, int64_t B) {
     Layout L;
     L.slots = 0;
     L.plans = align256(512 * (size_t)std::max<int64_t>(2 * nodes, 1));
-    L.totals = L.plans + align256(sizeof(VecPlan) * (size_t)std::max<int64_t>(B, 1));
+    L.bases = L.plans + align256(sizeof(VecPlan) * (size_t)std::max<int64_t>(B, 1));
+    L.totals = L.bases + align256(sizeof(int64_t) * (size_t)std::max<int64_t>(B, 1));
     L.cursor = L.totals + 256;
     L.end = L.cursor + 256;
     return L;
@@ -708,9 +728,10 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
 }
 
 // (for segments that may overlap, the plan kernel's overflow guard applies)
-static int64_t batch_nodes_bound(const nrm_ctx *c, int64_t x_len, int64_t B, int P) {
+static int64_t batch_nodes_bound(const nrm_ctx *c, int64_t x_len, int64_t B, int P, bool per_vector_p = false) {
     // sum over vectors of 2^dw - 1 < 2 (m_v / 2^k) summed, m_v <= n_v/P + 1
-    const int k = c->tune[P == 64 ? NRM_F64 : NRM_F32].item_log2;
+    // (with a p per vector, v1_lp items are LP_FINER levels smaller)
+    const int k = std::max(0, c->tune[P == 64 ? NRM_F64 : NRM_F32].item_log2 - (per_vector_p ? LP_FINER : 0));
     const int64_t rows = x_len / P + B + 1;
     return (2 * rows >> k) + 2;
 }
@@ -752,12 +773,13 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
                             int64_t B, T p, const double *p_dev, T *out, int32_t *status, cudaStream_t s,
                             T *lanes = nullptr) {
     constexpr int P = Geo<T>::P;
-    const int64_t nodes_bound = batch_nodes_bound(c, x_len, B, P);
+    const int64_t nodes_bound = batch_nodes_bound(c, x_len, B, P, p_dev != nullptr);
     Layout L = layout_for(nodes_bound, B);
     nrm_status st = nrm_ctx_ensure(c, L.end, nodes_bound);
     if (st != NRM_OK) return st;
     char *ws = (char *)c->ws;
     VecPlan *plans = reinterpret_cast<VecPlan *>(ws + L.plans);
+    int64_t *bases = reinterpret_cast<int64_t *>(ws + L.bases);
     int64_t *totals = reinterpret_cast<int64_t *>(ws + L.totals);
     unsigned long long *cursor = reinterpret_cast<unsigned long long *>(ws + L.cursor);
     const nrm_tuning &tu = tune_of<T>(c);
@@ -773,13 +795,14 @@ static nrm_status run_batch(nrm_ctx *c, const T *x, int64_t x_len, const int64_t
         kmax = std::max(kmax, tu.group_log2);
     }
     plan_kernel<T><<<1, 1024, 0, s>>>(off, lens, p_dev, B, x_len, tu.item_log2, DW_MAX, kmax, nodes_bound, plans,
-                                      totals, cursor, out, status);
+                                      bases, totals, cursor, out, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_cuda_err(c, e, "plan_kernel launch");
     TreeArgs<T> a{};
     a.x = x;
     a.out = out;
     a.plans = plans;
+    a.bases = bases;
     a.B = B;
     a.total_items = totals;
     a.cursor = cursor;
