@@ -234,8 +234,11 @@ nrm_status nrm_batch_segments(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int6
  * The same batch captured once into a CUDA graph (plan kernel + tree
  * kernel) and replayed with nrm_graph_launch; each replay reads the current
  * contents of x, offsets and p_dev (when not NULL).  The context's workspace
- * is sized for x_len and B at capture time.  *graph receives an opaque
- * handle owned by ctx.
+ * is sized for x_len and B at capture time; if later calls on the context
+ * grow its workspace, the buffers the graph was captured with stay
+ * allocated until the context is destroyed, so the graph remains valid (do
+ * not replay it concurrently with other calls on the same context).  *graph
+ * receives an opaque handle owned by ctx.
  */
 typedef struct nrm_graph nrm_graph;
 nrm_status nrm_batch_graph(nrm_ctx *ctx, nrm_dtype dtype, const void *x, int64_t x_len, const int64_t *offsets,

@@ -34,6 +34,9 @@ struct nrm_ctx {
     std::string err;
     uint64_t launches = 0;
     std::vector<nrm_graph *> graphs;
+    // buffers outgrown while graphs existed: a captured graph keeps their
+    // addresses, so they are freed with the context, not on growth
+    std::vector<void *> retired;
     // end-to-end (host buffer) staging
     void *stage = nullptr;
     size_t stage_bytes = 0;

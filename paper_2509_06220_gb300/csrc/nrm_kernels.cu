@@ -29,7 +29,15 @@ using namespace nrm;
 // Grow the workspace to `bytes` and the ticket array to `tickets` counters.
 // Tickets are zeroed when allocated and are returned to zero by every call
 // (each node's second arriver resets its ticket), so they never need
-// clearing between calls.
+// clearing between calls.  A captured graph holds the addresses of the
+// buffers it was captured with, so while the context has graphs an outgrown
+// buffer is retired (freed with the context) instead of freed.
+static void release_buffer(nrm_ctx *c, void *p) {
+    if (!p) return;
+    if (c->graphs.empty()) cudaFree(p);
+    else c->retired.push_back(p);
+}
+
 nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes, int64_t tickets) {
     if (bytes <= c->ws_bytes && tickets <= c->tickets_cap) return NRM_OK;
     cudaError_t e = cudaSetDevice(c->device);
@@ -37,7 +45,7 @@ nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes, int64_t tickets) {
     e = cudaDeviceSynchronize(); // the old buffers may still be in use
     if (e != cudaSuccess) return set_cuda_err(c, e, "cudaDeviceSynchronize");
     if (bytes > c->ws_bytes) {
-        if (c->ws) cudaFree(c->ws);
+        release_buffer(c, c->ws);
         c->ws = nullptr;
         c->ws_bytes = 0;
         size_t want = std::max(bytes, (size_t)1 << 20);
@@ -51,7 +59,7 @@ nrm_status nrm_ctx_ensure(nrm_ctx *c, size_t bytes, int64_t tickets) {
         c->ws_bytes = want;
     }
     if (tickets > c->tickets_cap) {
-        if (c->tickets) cudaFree(c->tickets);
+        release_buffer(c, c->tickets);
         c->tickets = nullptr;
         c->tickets_cap = 0;
         int64_t want = std::max<int64_t>(tickets, 1 << 16);
@@ -110,6 +118,7 @@ extern "C" nrm_status nrm_destroy(nrm_ctx *ctx) {
     if (ctx->tickets) cudaFree(ctx->tickets);
     if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->node_args) cudaFree(ctx->node_args);
+    for (void *p : ctx->retired) cudaFree(p);
     delete ctx;
     return NRM_OK;
 }

@@ -357,6 +357,47 @@ template <typename T> __device__ __forceinline__ bool plan_op(double pd, VecPlan
 
 constexpr int LP_FINER = 2;
 
+// Inclusive scan of v over the 1024 threads of the block (warp shuffles,
+// then the 32 warp totals); *total receives the block's sum.  s_warp: 32
+// shared slots.  Every thread of the block must call it.
+__device__ __forceinline__ int64_t block_scan_1024(int64_t v, int64_t *s_warp, int64_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) v += s_warp[warp - 1];
+    *total = s_warp[31];
+    __syncthreads(); // s_warp may be reused
+    return v;
+}
+
+// plans are stored as six 16-byte words (VecPlan is padded to 96 bytes)
+__device__ __forceinline__ void store_plan(VecPlan *dst, const VecPlan &pl) {
+    static_assert(sizeof(VecPlan) == 96, "VecPlan is six 16-byte words");
+    const int4 *src = reinterpret_cast<const int4 *>(&pl);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+#pragma unroll
+    for (int w = 0; w < 6; ++w) __stcg(d + w, src[w]);
+}
+
+// One block of 1024 threads.  Thread t handles vectors t, t + 1024, ...
+// (rounds), so that the offset loads and the status and output stores of a
+// warp are coalesced; prefix sums over the vectors run round by round with
+// the running totals carried along.
 template <typename T>
 __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ off, const int64_t *__restrict__ lens,
                                                     const double *__restrict__ pdev, int64_t B, int64_t x_len,
@@ -365,10 +406,9 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
                                                     unsigned long long *cursor,
                                                     T *out, int32_t *status) {
     constexpr int P = Geo<T>::P;
-    __shared__ int64_t s_items[1024], s_nodes[1024];
+    __shared__ int64_t s_warp[32];
     const int tid = threadIdx.x;
-    const int64_t per = (B + blockDim.x - 1) / blockDim.x;
-    const int64_t v0 = min(B, tid * per), v1 = min(B, v0 + per);
+    const int64_t rounds = (B + 1023) / 1024;
     int kk = kitem; // work-item depth; deepened below if the tickets would not fit
     auto plan_of = [&](int64_t v, VecPlan &pl, int64_t &items, int64_t &nodes, int32_t &st) {
         const int64_t a = off[v];
@@ -402,65 +442,47 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         items = int64_t(1) << pl.dw;
         nodes = items - 1;
     };
-    int64_t si, sn;
+    // totals; segments may overlap, so their nodes are not bounded by x_len:
+    // deeper work items need fewer tickets (the tree is unchanged)
+    int64_t total_items, total_nodes;
     for (;;) {
-        si = 0;
-        sn = 0;
-        for (int64_t v = v0; v < v1; ++v) {
-            VecPlan pl;
-            int64_t it, nd;
-            int32_t st;
-            plan_of(v, pl, it, nd, st);
-            si += it;
-            sn += nd;
-        }
-        s_items[tid] = si;
-        s_nodes[tid] = sn;
-        __syncthreads();
-        // Hillis-Steele inclusive scan over the 1024 partial sums
-        for (int d = 1; d < 1024; d <<= 1) {
-            int64_t ai = 0, an = 0;
-            if (tid >= d) {
-                ai = s_items[tid - d];
-                an = s_nodes[tid - d];
+        int64_t ti = 0, tn = 0;
+        for (int64_t r = 0; r < rounds; ++r) {
+            const int64_t v = r * 1024 + tid;
+            int64_t it = 0, nd = 0;
+            if (v < B) {
+                VecPlan pl;
+                int32_t st;
+                plan_of(v, pl, it, nd, st);
             }
-            __syncthreads();
-            s_items[tid] += ai;
-            s_nodes[tid] += an;
-            __syncthreads();
+            int64_t si, sn;
+            block_scan_1024(it, s_warp, &si);
+            block_scan_1024(nd, s_warp, &sn);
+            ti += si;
+            tn += sn;
         }
-        // segments may overlap, so their nodes are not bounded by x_len:
-        // deeper work items need fewer tickets (the tree is unchanged)
-        if (s_nodes[blockDim.x - 1] <= node_cap || kk >= kmax) break;
-        __syncthreads();
+        total_items = ti;
+        total_nodes = tn;
+        if (total_nodes <= node_cap || kk >= kmax) break;
         ++kk;
     }
     // If even the deepest work items need more ticket nodes than the
     // workspace holds, no vector is computed and all report NRM_ENOMEM.
-    const bool overflow = s_nodes[blockDim.x - 1] > node_cap;
-    const int64_t total_items = s_items[blockDim.x - 1], total_nodes = s_nodes[blockDim.x - 1];
-    const int64_t nb0 = s_nodes[tid] - sn; // this thread's first ticket node (vector order)
-    const int64_t ib0 = s_items[tid] - si; // its first work item in vector order
+    const bool overflow = total_nodes > node_cap;
     // Work order: the persistent grid takes work items in index order, so
     // the vectors are numbered longest first: a counting sort on n in
     // quarter-octave classes (floor(log2 n) and its next two bits; the last
     // class for vectors without work items), the plans stored in that order
     // with their output index, and their item bases increasing with the
     // plan index.  With a p per vector the classes are ordered by combine
-    // first (v1_lp, v1_hypot, maxabs, sumabs: the costliest first), so that
-    // the warps of an SM mostly run one combine's code at a time (interleaved
-    // combines thrashed the instruction cache: 6.65 ms against 3.5 ms for the
-    // same batch split by p).  Within a class the order comes from
-    // warp-aggregated shared-memory atomics, so it may differ between calls:
-    // it decides which warp computes a subtree, never the tree.  Ticket nodes
-    // keep the vector order.  Every thread runs the same number of
-    // iterations (per), so the warp-wide match and shuffles see converged
-    // warps.
+    // first (v1_lp, v1_hypot, maxabs, sumabs: the costliest first).  Within
+    // a class the order comes from warp-aggregated shared-memory atomics, so
+    // it may differ between calls: it decides which warp computes a subtree,
+    // never the tree.  Ticket nodes keep the vector order.
     constexpr int NL = 4 * 41 + 1;   // length classes
-    constexpr int NB = 4 * NL;       // (combine, length) classes
+    constexpr int NB = 4 * NL;       // (combine, length) classes, NB <= 1024
     __shared__ unsigned s_cnt[NB], s_cur[NB];
-    __shared__ int64_t s_vbase[1024];
-    const bool sorted = B < (int64_t(1) << 31);
+    __shared__ int64_t s_vbase[NB];
     auto bucket_of = [&](const VecPlan &pl, int64_t items) {
         if (items == 0 || overflow) return NB - 1;
         const int64_t n = pl.n;
@@ -471,13 +493,12 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     };
     const int lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u; // lanes below this one
-    __syncthreads(); // every reader of the scans above is done
-    for (int q = tid; q < NB; q += blockDim.x) s_cnt[q] = s_cur[q] = 0u;
+    for (int q = tid; q < NB; q += 1024) s_cnt[q] = s_cur[q] = 0u;
     __syncthreads();
     // statuses, the outputs of empty or bad vectors, and the class counts
-    for (int64_t r = 0; r < per; ++r) {
-        const int64_t v = v0 + r;
-        const bool valid = v < v1;
+    for (int64_t r = 0; r < rounds; ++r) {
+        const int64_t v = r * 1024 + tid;
+        const bool valid = v < B;
         int q = NB; // no class
         if (valid) {
             VecPlan pl;
@@ -490,32 +511,23 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
             else if (pl.n == 0) out[v] = T(0);
             q = bucket_of(pl, it);
         }
-        if (sorted) {
-            const unsigned grp = __match_any_sync(FULL, q);
-            if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
-        }
+        const unsigned grp = __match_any_sync(FULL, q);
+        if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
     }
     __syncthreads();
     // first plan index of every class: an exclusive scan over the classes
-    if (sorted) {
+    {
         const int64_t c = tid < NB ? (int64_t)s_cnt[tid] : 0;
-        s_vbase[tid] = c;
-        __syncthreads();
-        for (int d = 1; d < 1024; d <<= 1) {
-            const int64_t a = tid >= d ? s_vbase[tid - d] : 0;
-            __syncthreads();
-            s_vbase[tid] += a;
-            __syncthreads();
-        }
-        s_vbase[tid] -= c;
+        int64_t tot;
+        const int64_t incl = block_scan_1024(c, s_warp, &tot);
+        if (tid < NB) s_vbase[tid] = incl - c;
         __syncthreads();
     }
-    // the plans: in class order (their item counts in item_base for now), or
-    // in vector order with their item bases
-    int64_t nbr = nb0, ib_unsorted = ib0;
-    for (int64_t r = 0; r < per; ++r) {
-        const int64_t v = v0 + r;
-        const bool valid = v < v1;
+    // the plans, in class order, with their item counts in item_base for now
+    int64_t nbase = 0; // ticket nodes of the earlier rounds
+    for (int64_t r = 0; r < rounds; ++r) {
+        const int64_t v = r * 1024 + tid;
+        const bool valid = v < B;
         VecPlan pl;
         int64_t it = 0, nd = 0;
         int q = NB;
@@ -523,51 +535,38 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
             int32_t st;
             plan_of(v, pl, it, nd, st);
             if (overflow) it = 0;
-            pl.node_base = nbr;
-            pl.out_idx = v;
-            nbr += nd;
             q = bucket_of(pl, it);
         }
-        if (sorted) {
-            const unsigned grp = __match_any_sync(FULL, q);
-            const int leader = __ffs(grp) - 1;
-            unsigned base = 0u;
-            if (valid && lane == leader) base = atomicAdd(&s_cur[q], (unsigned)__popc(grp));
-            base = __shfl_sync(FULL, base, leader);
-            if (valid) {
-                pl.item_base = it;
-                plans[s_vbase[q] + base + __popc(grp & lt)] = pl;
-            }
-        } else if (valid) {
-            pl.item_base = ib_unsorted;
-            plans[v] = pl;
-            bases[v] = ib_unsorted;
-            ib_unsorted += it;
+        int64_t sn;
+        const int64_t incl = block_scan_1024(nd, s_warp, &sn);
+        const unsigned grp = __match_any_sync(FULL, q);
+        const int leader = __ffs(grp) - 1;
+        unsigned base = 0u;
+        if (valid && lane == leader) base = atomicAdd(&s_cur[q], (unsigned)__popc(grp));
+        base = __shfl_sync(FULL, base, leader);
+        if (valid) {
+            pl.node_base = nbase + incl - nd;
+            pl.out_idx = v;
+            pl.item_base = it;
+            store_plan(plans + s_vbase[q] + base + __popc(grp & lt), pl);
         }
+        nbase += sn;
     }
-    if (sorted) {
-        // item bases in plan order: a block scan over the plans' item counts
-        __syncthreads(); // the plans are written (visible within the block)
-        int64_t cnt = 0;
-        for (int64_t s = v0; s < v1; ++s) cnt += plans[s].item_base;
-        __syncthreads();
-        s_items[tid] = cnt;
-        __syncthreads();
-        for (int d = 1; d < 1024; d <<= 1) {
-            const int64_t a = tid >= d ? s_items[tid - d] : 0;
-            __syncthreads();
-            s_items[tid] += a;
-            __syncthreads();
+    __syncthreads(); // the plans are written (visible within the block)
+    // item bases in plan order, round by round
+    int64_t ibase = 0;
+    for (int64_t r = 0; r < rounds; ++r) {
+        const int64_t s = r * 1024 + tid;
+        const int64_t c = s < B ? plans[s].item_base : 0;
+        int64_t tot;
+        const int64_t incl = block_scan_1024(c, s_warp, &tot);
+        if (s < B) {
+            plans[s].item_base = ibase + incl - c;
+            bases[s] = ibase + incl - c;
         }
-        int64_t ib = s_items[tid] - cnt;
-        for (int64_t s = v0; s < v1; ++s) {
-            const int64_t c = plans[s].item_base;
-            plans[s].item_base = ib;
-            bases[s] = ib;
-            ib += c;
-        }
+        ibase += tot;
     }
-    if (tid == blockDim.x - 1) {
+    if (tid == 0) {
         totals[0] = overflow ? 0 : total_items;
         totals[1] = total_nodes;
         *cursor = 0ull;

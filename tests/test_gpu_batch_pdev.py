@@ -125,3 +125,28 @@ def test_segments_per_vector_p(nrm):
     for i in range(250):
         want = oracle.nrm(x[starts[i]:starts[i] + lens[i]], dt(p[i]))
         assert o[i].tobytes() == want.tobytes(), (i, p[i], lens[i])
+
+
+def test_graphs_survive_workspace_growth(nrm):
+    """A graph keeps the workspace it was captured with: capturing a second
+    batch that needs a larger workspace (a p per vector sizes its tickets for
+    finer v1_lp items), then a long single vector, grows the context's
+    workspace, and both graphs still replay correctly."""
+    dt = np.float64
+    x, off, p = _case(150, 81, dt, max_log2=13)
+    xd, offd, pd = torch.from_numpy(x).to(DEV), torch.from_numpy(off).to(DEV), torch.from_numpy(p).to(DEV)
+    ctx = nrm.Context(0)
+    try:
+        g1 = nrm.nrm_batch_graph(xd, offd, 2.0, ctx=ctx)
+        g2 = nrm.nrm_batch_graph(xd, offd, pd, ctx=ctx)
+        big = nrm.nrm_gen((1 << 24) + 3, 82, 0, torch.float64, device=DEV)
+        nrm.nrmf(big, ctx=ctx)
+        o1, s1 = g1.launch()
+        o2, s2 = g2.launch()
+        torch.cuda.synchronize()
+        assert o1.cpu().numpy().tobytes() == _want(x, off, np.full(p.size, 2.0), dt).tobytes()
+        assert o2.cpu().numpy().tobytes() == _want(x, off, p, dt).tobytes()
+        g1.close()
+        g2.close()
+    finally:
+        ctx.close()

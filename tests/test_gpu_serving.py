@@ -56,7 +56,8 @@ def test_batch_segments_any_order(nrm, dt):
 def test_server_results_equal_alone(nrm):
     """A bursty mixed trace (FP32/FP64, p in {2, 1.5, 3}, lengths in
     [16, 2^17]) through 2 streams with batching: each norm equals the
-    request computed alone; host-provided inputs too."""
+    request computed alone and the oracle's norm of the same input; host-
+    provided inputs too."""
     tr = nrm.serving_trace(200000, 0.004, seed=5, max_log2=17)
     srv = nrm.Server(budget_bytes=1 << 30, nstreams=2, max_batch=256)
     try:
@@ -71,6 +72,11 @@ def test_server_results_equal_alone(nrm):
             r = tr[i]
             want = alone(nrm, i, r.n, r.dtype, r.p, r.seed)
             assert same(norms[i], want), (i, r.n, r.dtype, r.p, norms[i], want)
+            # and the oracle on the same input, regenerated on the host from
+            # (seed, request id)
+            dt = np.float64 if r.dtype == nrm.NRM_F64 else np.float32
+            x = inputs.vector(r.n, seed=r.seed, vec=i, dtype=dt, emin=-20, emax=20)
+            assert same(norms[i], float(oracle.nrm(x, r.p))), (i, r.n, r.dtype, r.p)
         # host inputs mixed with generated ones
         xs = [inputs.vector(n, seed=31, vec=j, dtype=dt) for j, (n, dt) in
               enumerate([(1000, np.float64), (77777, np.float32), (5, np.float64), (0, np.float32)])]
