@@ -440,6 +440,17 @@ nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned
  * arrays or an unknown dtype. */
 nrm_status nrm_test_pow(nrm_dtype dtype, const void *x, const void *y, void *out, int64_t n, void *stream);
 
+/* Test hook: the binary64 pow that v1_lp uses for 1 < p <= 2^17 (Listing 5,
+ * Section 4, with the pow restricted to the two domains of v1_lp: x in
+ * [0, 1) with y in [1/2, 2^16], or x in [1, 2] with y in [2^-17, 1]; a result
+ * below 2^-28 is returned as +0), elementwise out[i] = pow(x[i], y[i]) with
+ * the device code of the xNRMP tree kernels.  x, y and out are device
+ * arrays of n binary64 values; the caller keeps the operands in that
+ * domain (outside it the values are unspecified, nothing is read or
+ * written beyond the n elements).  Asynchronous on `stream`; NRM_EINVAL for
+ * n < 0 or null arrays. */
+nrm_status nrm_test_powr(const double *x, const double *y, double *out, int64_t n, void *stream);
+
 /* Test hook: v1_lp (Listing 5, Section 4's Eq. sp) elementwise with
  * h = p/2 and ip = 1/p rounded in `dtype`, out[i] = v1_lp(x[i], y[i]),
  * exactly as the xNRMP tree kernels combine (for binary64 the integer

@@ -37,6 +37,9 @@ def lib():
             "or_lp_s": (f, [f, f, f, f]),
             "or_pow_arr_d": (None, [i64, vp, vp, vp]),
             "or_pow_arr_s": (None, [i64, vp, vp, vp]),
+            "or_powr_d": (d, [d, d]),
+            "or_powr_arr_d": (None, [i64, vp, vp, vp]),
+            "or_powr_table_d": (None, [vp]),
             "or_lp_arr_d": (None, [i64, d, d, vp, vp, vp]),
             "or_lp_arr_s": (None, [i64, f, f, vp, vp, vp]),
             "or_comb_arr_d": (None, [i64, d, vp, vp, vp]),
@@ -111,6 +114,27 @@ def pow_arr(x, y):
     out = np.empty(xa.shape, dt)
     f = lib().or_pow_arr_d if dt == np.float64 else lib().or_pow_arr_s
     f(xa.size, xp, yp, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def powr_arr(x, y):
+    """Elementwise or_powr_d (the binary64 pow of v1_lp for 1 < p <= 2^17)
+    over two float64 arrays."""
+    xa, xp = _arr(x, np.float64)
+    ya, yp = _arr(y, np.float64)
+    out = np.empty(xa.shape, np.float64)
+    lib().or_powr_arr_d(xa.size, xp, yp, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def powr_table():
+    """or_powr_d's Q96 logarithm table T1q_j as Python ints."""
+    t = np.zeros(512, np.uint64)
+    lib().or_powr_table_d(t.ctypes.data_as(ctypes.c_void_p))
+    out = []
+    for j in range(256):
+        v = int(t[2 * j]) << 64 | int(t[2 * j + 1])
+        out.append(v - (1 << 128) if v >> 127 else v)
     return out
 
 

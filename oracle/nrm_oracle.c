@@ -25,6 +25,9 @@
  *                          and exp: binary64 in exact fixed-point integer
  *                          arithmetic, binary32 with double-word (Dekker)
  *                          arithmetic.
+ *   or_powr_d              the binary64 pow of v1_lp for 1 < p <= 2^17,
+ *                          restricted to its two operand ranges (log2 x in
+ *                          plain Q96 fixed point, results below 2^-28 as 0)
  *   or_R_*                 R_x, Listing 1 / Eq. r (Section 2)
  *   or_Z_*                 Z_x generalised to p lanes, Listing 4 (Section 3)
  *   or_nrm_*               xNRMF / xNRMP = Z then a final R over the lanes
@@ -459,6 +462,7 @@ static uint32_t pw_r1(int j)
 }
 
 static i128 PW_T1[256];            /* Q88 */
+static i128 PW_T1Q96[256];         /* the same logarithms in Q96, for or_powr_d */
 static i128 PW_T2[2 * PW_J2MAX + 1]; /* Q96, index j2 + PW_J2MAX */
 static uint64_t PW_TE[256];        /* Q63 */
 static pthread_once_t pw_once = PTHREAD_ONCE_INIT;
@@ -472,6 +476,7 @@ static void pw_init(void)
     for (int j = 0; j < 256; ++j) {
         const q128 r1 = (q128)pw_r1(j);
         PW_T1[j] = q_round(Q_LOG2((j < 128 ? (q128)512 : (q128)256) / r1) * two88);
+        PW_T1Q96[j] = q_round(Q_LOG2((j < 128 ? (q128)512 : (q128)256) / r1) * two96);
     }
     for (int j2 = -PW_J2MAX; j2 <= PW_J2MAX; ++j2)
         PW_T2[j2 + PW_J2MAX] = q_round(-Q_LOG2((q128)1 - (q128)j2 / (q128)65536) * two96);
@@ -620,6 +625,117 @@ OR_API double or_pow_d(double x, double y)
 }
 
 /*
+ * or_powr_d(x, y): the pow of v1_lp for 1 < p <= 2^17 in binary64.  Its two
+ * calls there are S = pow(Q, p/2), Q in [0, 1], p/2 in (1/2, 2^16], and
+ * C = pow(Z, 1/p), Z in [1, 2], 1/p in [2^-17, 1); this is the domain:
+ * 0 <= x < 1 with 1/2 <= y <= 2^16, or 1 <= x <= 2 with 2^-17 <= y <= 1.
+ * Steps 1-3 and 7-8 are those of or_pow_d; log2 x and t = y log2 x are
+ * formed differently, in plain fixed point, which the bound on y allows:
+ *  4'. log2(1 + u), u = U2 2^-77, in Q96 from the series of ln(1 + u) to
+ *      u^5 with the factor 1/ln 2 taken into the coefficients (the u^6
+ *      term is below 2^-94): with a = |U2|,
+ *        A1 = a D1 2^-76 (D1 = RN(2^95/ln 2), 96 bits, as D1h 2^32 + D1l:
+ *             floor(a D1h / 2^44) + floor(a D1l / 2^76)),  |u|/ln 2
+ *        sq = floor(a^2 / 2^64) (u^2 in Q90),
+ *        A2 = floor(sq D2 / 2^64) 2^6 (D2 = RN(2^63/ln 2)),   u^2/(2 ln 2)
+ *        cu = floor(sq a / 2^64) (|u|^3 in Q103),
+ *        A3 = floor(floor(cu D3 / 2^64) / 2^7) (D3 = RN(2^64/(3 ln 2))),
+ *        q4 = floor(sq/2^32)^2 (u^4 in Q116),
+ *        A4 = floor(floor(q4/2^32) D4 / 2^20) (D4 = RN(2^32/(4 ln 2))),
+ *        A5 = floor(floor(floor(q4/2^32) floor(a/2^32) / 2^32) D5 / 2^33)
+ *             (D5 = RN(2^32/(5 ln 2))),
+ *      and log2(1 + u) = A1 - A2 + A3 - A4 + A5 for u >= 0, -(A1 + A2 + A3
+ *      + A4 + A5) for u < 0 (error below 2^-85).
+ *  5'. W = E 2^96 + T1q_j + T2_j2 + log2(1 + u) = log2 x in Q96, T1q_j =
+ *      RN(log2(2^9/r1_j) 2^96) (j < 128) or RN(log2(2^8/r1_j) 2^96).
+ *  6'. y = Y 2^ey (Y the 53-bit significand): t 2^64 = sign(W) floor(Y |W|
+ *      / 2^(32 - ey)) (|y| <= 2^16 keeps the error of W below 2^-69 in t).
+ *  7-8 as or_pow_d with k = floor(t); the result is needed only in
+ *      [2^-28, 2]: S below 2^-27 gives RN(1 + S^2) = 1 whatever S is, so
+ *      k < -28 returns +0, and so does x < 2^-60 (t < -30 there).
+ * The error before the final rounding stays below 2^-62 relative.  Exact
+ * cases: pow(0, y) = 0, pow(1, y) = 1, and x = 2^a with ay an integer.
+ */
+#define PR_D1H 0xb8aa3b295c17f0bbull /* RN(2^95/ln 2) = PR_D1H 2^32 + PR_D1L */
+#define PR_D1L 0xbe87fed0ull
+#define PR_D2 0xb8aa3b295c17f0bcull  /* RN(2^63/ln 2) */
+#define PR_D3 0x7b1c2770e80ff5d2ull  /* RN(2^64/(3 ln 2)) */
+#define PR_D4 0x5c551d95ull          /* RN(2^32/(4 ln 2)) */
+#define PR_D5 0x49ddb144ull          /* RN(2^32/(5 ln 2)) */
+
+OR_API double or_powr_d(double x, double y)
+{
+    if (x == 0.0) return 0.0;
+    if (x == 1.0) return 1.0;
+    pthread_once(&pw_once, pw_init);
+    /* step 1 */
+    uint64_t M;
+    int E;
+    decompose_d(x, &M, &E);
+    E += 52;
+    const int j = (int)((M >> 44) & 255);
+    if (j >= 128) E += 1;
+    if (E < -60) return 0.0;
+    /* steps 2 and 3 */
+    const int64_t U1 = (int64_t)(M * (uint64_t)pw_r1(j) - (1ull << 61));
+    const int64_t j2 = (U1 + ((int64_t)1 << 44)) >> 45;
+    const int64_t U2 = (int64_t)((uint64_t)(U1 - j2 * ((int64_t)1 << 45)) << 16) - U1 * j2;
+    /* step 4' */
+    const uint64_t a = U2 < 0 ? (uint64_t)(-U2) : (uint64_t)U2;
+    const u128 A1 = (((u128)a * PR_D1H) >> 44) + (((u128)a * PR_D1L) >> 76);
+    const uint64_t sq = (uint64_t)(((u128)a * a) >> 64);
+    const u128 A2 = (u128)(uint64_t)(((u128)sq * PR_D2) >> 64) << 6;
+    const uint64_t cu = (uint64_t)(((u128)sq * a) >> 64);
+    const uint64_t A3 = (uint64_t)(((u128)cu * PR_D3) >> 64) >> 7;
+    const uint64_t s32 = sq >> 32;
+    const uint64_t q4h = (s32 * s32) >> 32;
+    const uint64_t A4 = (q4h * PR_D4) >> 20;
+    const uint64_t A5 = (((q4h * (a >> 32)) >> 32) * PR_D5) >> 33;
+    const i128 l = U2 < 0 ? -(i128)(A1 + A2 + A3 + A4 + A5) : (i128)(A1 + A3 + A5) - (i128)(A2 + A4);
+    /* step 5' */
+    const i128 W = (i128)E * ((i128)1 << 96) + PW_T1Q96[j] + PW_T2[j2 + PW_J2MAX] + l;
+    /* step 6' */
+    uint64_t Ym;
+    int ey;
+    decompose_d(y, &Ym, &ey);
+    const u128 aW = W < 0 ? (u128)(-W) : (u128)W;
+    const u128 p0 = (u128)Ym * (uint64_t)aW;
+    const u128 p1 = (u128)Ym * (uint64_t)(aW >> 64);
+    u192 Pt;
+    Pt.lo = p0 + (p1 << 64);
+    Pt.hi = (uint64_t)(p1 >> 64) + (Pt.lo < p0);
+    const u128 T64 = u192_shr(Pt, 32 - ey);
+    const i128 tq = W < 0 ? -(i128)T64 : (i128)T64;
+    /* step 7 */
+    const int k = (int)(tq >> 64);
+    if (k < -28) return 0.0;
+    const uint64_t r = (uint64_t)tq;
+    const int i = (int)(r >> 56);
+    const uint64_t rho = r & ((1ull << 56) - 1);
+    const uint64_t v70 = (uint64_t)(((u128)rho * PW_LN2) >> 58);
+    const uint32_t v32 = (uint32_t)(v70 >> 38); /* v in Q32 */
+    uint32_t e32 = (uint32_t)((1ull << 32) / 720);
+    e32 = (uint32_t)((1ull << 32) / 120) + mulhi32(e32, v32);
+    e32 = (uint32_t)((1ull << 32) / 24) + mulhi32(e32, v32); /* Q32 */
+    uint64_t Ev = (uint64_t)e32 << 31;                         /* Q63 */
+    Ev = (1ull << 63) / 6 + (mulhi64(Ev, v70) >> 6);
+    Ev = (1ull << 62) + (mulhi64(Ev, v70) >> 6);
+    Ev = (1ull << 63) + (mulhi64(Ev, v70) >> 6);
+    Ev = (1ull << 63) + (mulhi64(Ev, v70) >> 6);
+    const u128 P = (u128)PW_TE[i] * Ev; /* Q126, in [2^126, 2^128) */
+    /* step 8: a normal result (k in [-28, 1]) */
+    const int nb = 128 - clz64((uint64_t)(P >> 64));
+    int Er = k + nb - 127;
+    uint64_t m = (uint64_t)rne_shr(P, nb - 53);
+    if (m >> 53) { m >>= 1; Er += 1; }
+    return from_bits_d(((uint64_t)(Er + 1023) << 52) | (m & 0x000fffffffffffffull));
+}
+
+/* or_powr_d serves v1_lp's pows when p/2 lies in (1/2, 2^16], i.e. for
+ * 1 < p <= 2^17; other p (quasi-norms p < 1, very large p) take or_pow_d. */
+static int powr_covers_d(double h) { return h > 0.5 && h <= 0x1p16; }
+
+/*
  * or_pow_s(x, y) ~ x^y in binary32, the powf of Listing 5 for S; the same
  * five steps as or_pow_d with binary32 double-word arithmetic: atanh series
  * to z^5/13 and the exp series to degree 9.
@@ -700,7 +816,8 @@ OR_API float or_pow_s(float x, float y)
 
 /* v1_lp (Listing 5, Section 4): Eq. sp with the Eq. qp trick of squaring
  * pow(Q, p/2) inside an fma.  h = p*0.5 and ip = 1.0/p are computed once per
- * call (Section 4 hoists them to the top of the recursion). */
+ * call (Section 4 hoists them to the top of the recursion).  Both pows are
+ * or_powr_d for 1 < p <= 2^17 (h in (1/2, 2^16]), or_pow_d otherwise. */
 OR_API double or_lp_d(double h, double ip, double x, double y)
 {
     const double X = fabs(x);
@@ -709,9 +826,10 @@ OR_API double or_lp_d(double h, double ip, double x, double y)
     const double M = max_d(X, Y);
     const double q = m / M;
     const double Q = max_d(q, 0.0);
-    const double S = or_pow_d(Q, h);
+    const int r = powr_covers_d(h);
+    const double S = r ? or_powr_d(Q, h) : or_pow_d(Q, h);
     const double Z = fma(S, S, 1.0);
-    const double C = or_pow_d(Z, ip);
+    const double C = r ? or_powr_d(Z, ip) : or_pow_d(Z, ip);
     return M * C;
 }
 
@@ -735,6 +853,21 @@ OR_API float or_lp_s(float h, float ip, float x, float y)
 OR_API void or_pow_arr_d(int64_t n, const double *x, const double *y, double *out)
 {
     for (int64_t i = 0; i < n; ++i) out[i] = or_pow_d(x[i], y[i]);
+}
+
+OR_API void or_powr_arr_d(int64_t n, const double *x, const double *y, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = or_powr_d(x[i], y[i]);
+}
+
+/* the Q96 logarithm table of or_powr_d, as two's complement {hi, lo} pairs */
+OR_API void or_powr_table_d(uint64_t *T1q)
+{
+    pthread_once(&pw_once, pw_init);
+    for (int j = 0; j < 256; ++j) {
+        T1q[2 * j] = (uint64_t)((u128)PW_T1Q96[j] >> 64);
+        T1q[2 * j + 1] = (uint64_t)(u128)PW_T1Q96[j];
+    }
 }
 
 OR_API void or_pow_arr_s(int64_t n, const float *x, const float *y, float *out)

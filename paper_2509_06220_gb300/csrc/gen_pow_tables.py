@@ -18,6 +18,13 @@ tables with mpmath at 400 bits and rounds each entry to nearest:
   ILN2  = RN(2^127 / ln 2), 128 bits
   LN2   = RN(2^64 ln 2)
 
+and for the pow of v1_lp with 1 < p <= 2^17 (powr_d), whose logarithm is
+formed in Q96 fixed point with 1/ln 2 taken into the series coefficients:
+
+  T1q_j = RN(log2(2^9 / r1_j) 2^96) (j < 128) or RN(log2(2^8 / r1_j) 2^96)
+  D1    = RN(2^95 / ln 2) (96 bits, as D1h 2^32 + D1l), D2 = RN(2^63 / ln 2),
+  D3    = RN(2^64 / (3 ln 2)), D4 = RN(2^32 / (4 ln 2)), D5 = RN(2^32 / (5 ln 2))
+
 Run from this directory: python gen_pow_tables.py (needs mpmath); the
 tests pin every entry of the written header against these definitions.
 """
@@ -53,6 +60,16 @@ def tables():
     return R1, T1, T2, TE, ILN2, LN2
 
 
+def powr_tables():
+    two = mpmath.mpf(2)
+    ln2 = mpmath.log(2)
+    R1 = [r1_of(j) for j in range(256)]
+    T1q = [rn(mpmath.log(mpmath.mpf(512 if j < 128 else 256) / R1[j], 2) * two ** 96) for j in range(256)]
+    D = {"D1": rn(two ** 95 / ln2), "D2": rn(two ** 63 / ln2), "D3": rn(two ** 64 / (3 * ln2)),
+         "D4": rn(two ** 32 / (4 * ln2)), "D5": rn(two ** 32 / (5 * ln2))}
+    return T1q, D
+
+
 def main():
     R1, T1, T2, TE, ILN2, LN2 = tables()
     M = (1 << 64) - 1
@@ -84,6 +101,18 @@ def main():
     for i in range(0, 256, 4):
         out.append("    " + " ".join("0x%016xull," % TE[k] for k in range(i, i + 4)))
     out.append("};")
+    T1q, D = powr_tables()
+    out.append("// T1q_j = RN(log2(2^9 or 2^8 / r1_j) 2^96) as a two's-complement 128-bit {high, low}")
+    out.append("static __device__ const uint64_t kPowT1Q96[256][2] = {")
+    for j in range(0, 256, 2):
+        out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (((T1q[k] >> 64) & M), T1q[k] & M) for k in (j, j + 1)))
+    out.append("};")
+    out.append("constexpr uint64_t kPrD1H = 0x%016xull; // RN(2^95 / ln 2) = kPrD1H 2^32 + kPrD1L" % (D["D1"] >> 32))
+    out.append("constexpr uint64_t kPrD1L = 0x%08xull;" % (D["D1"] & 0xFFFFFFFF))
+    out.append("constexpr uint64_t kPrD2 = 0x%016xull; // RN(2^63 / ln 2)" % D["D2"])
+    out.append("constexpr uint64_t kPrD3 = 0x%016xull; // RN(2^64 / (3 ln 2))" % D["D3"])
+    out.append("constexpr uint32_t kPrD4 = 0x%08xu; // RN(2^32 / (4 ln 2))" % D["D4"])
+    out.append("constexpr uint32_t kPrD5 = 0x%08xu; // RN(2^32 / (5 ln 2))" % D["D5"])
     out.append("constexpr int kPowJ2Max = %d;" % J2MAX)
     out.append("constexpr uint64_t kPowILN2_HI = 0x%016xull; // RN(2^127 / ln 2), high word" % (ILN2 >> 64))
     out.append("constexpr uint64_t kPowILN2_LO = 0x%016xull; // low word" % (ILN2 & M))

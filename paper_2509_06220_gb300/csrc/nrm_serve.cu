@@ -342,6 +342,12 @@ extern "C" nrm_status nrm_srv_create(nrm_srv **srv, int device, size_t budget_by
     for (Lane &ln : s->lanes) {
         st = nrm_create(&ln.ctx, device);
         if (st != NRM_OK) break;
+        // the steps' batches take items of 2^9 rows: the finer items of the
+        // single-vector defaults would multiply the slot workspace that is
+        // reserved below for every stream
+        const nrm_tuning bt[2] = {nrm_tuning{2, 4, 9, 16}, nrm_tuning{2, 8, 9, 16}};
+        nrm_set_tuning_for(ln.ctx, NRM_F32, &bt[0]);
+        nrm_set_tuning_for(ln.ctx, NRM_F64, &bt[1]);
         // reserve the largest workspace a step can need: every element of
         // the arena in one batch of the narrowest type (most rows)
         const int64_t max_elems = (int64_t)(budget_bytes / 4);

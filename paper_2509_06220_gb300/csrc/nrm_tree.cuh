@@ -57,6 +57,8 @@ template <typename T> struct TreeArgs {
     int64_t item_lo, item_hi;      // single vector: item range of this launch
     const int64_t *total_items;    // batch: written by the plan kernel
     unsigned long long *cursor;    // batch: dynamic work cursor (zeroed by plan)
+    unsigned *item_cursor;         // single vector: dynamic item cursor (zero between launches), or
+                                   // nullptr for a static assignment (warp w takes items w, w + nwarps, ...)
     unsigned *tickets;
     T *slots;
     int levels;                    // counter-stack rows per warp: max k - G of the launch
@@ -251,11 +253,22 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
     typename Geo<T>::vec *ring;
     warp_smem<T, G, StagesOf<Op>::value>(a, stk, ring);
 
+    // Work order.  Batch: the atomic cursor.  Single vector: items of one
+    // size, taken from the item cursor in index order, so that the last
+    // round of items spreads over all SMs (a static stride left whole SMs
+    // idle while others ran their last items); the warp that draws the last
+    // value (total - item_lo + nwarps - 1: every other draw happened before
+    // it) returns the cursor to zero for the next launch.
+    const bool dyn = !batch && a.item_cursor != nullptr;
     int64_t gi;
     if (batch) {
         unsigned long long g0 = 0;
         if (lane == 0) g0 = atomicAdd(a.cursor, 1ull);
         gi = (int64_t)__shfl_sync(FULL, g0, 0);
+    } else if (dyn) {
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(a.item_cursor, 1u);
+        gi = a.item_lo + (int64_t)__shfl_sync(FULL, g0, 0);
     } else {
         gi = a.item_lo + wglobal;
     }
@@ -273,18 +286,21 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
             unsigned long long g1 = 0;
             if (lane == 0) g1 = atomicAdd(a.cursor, 1ull);
             gi = (int64_t)__shfl_sync(FULL, g1, 0);
+        } else if (dyn) {
+            unsigned g1 = 0;
+            if (lane == 0) g1 = atomicAdd(a.item_cursor, 1u);
+            gi = a.item_lo + (int64_t)__shfl_sync(FULL, g1, 0);
         } else {
             gi += nwarps;
         }
     }
+    if (dyn && lane == 0 && gi - a.item_lo == total - a.item_lo + nwarps - 1) *a.item_cursor = 0u;
 }
 
 // A ragged batch with a p per vector: the same persistent loop, each work
 // item combined with its vector's op (a warp-uniform switch: an item belongs
 // to one vector), so every result is bitwise that of the single-p kernel for
-// that vector's p.  Register cap: binary64 takes v1_hypot's (64; most of a
-// serving mix is p = 2, and v1_lp loses nothing there: the config-2 batch
-// with p = 3 took 7.67 ms against 8.13 ms in the one-p kernel at 128);
+// that vector's p.  Register cap: binary64 64, the cap of all its ops;
 // binary32 takes v1_lp's (at v1_hypot's 72 the binary32 v1_lp spills:
 // 2.33 ms against 1.46 ms).
 template <typename T> struct MixedRegs {
@@ -309,8 +325,7 @@ __global__ void __maxnreg__(MixedRegs<T>::value) tree_kernel_mixed(TreeArgs<T> a
             break;
         case OP_LP: {
             OpLp<T> o;
-            o.h = (T)pl.h;
-            o.ip = (T)pl.ip;
+            o.set((T)pl.h, (T)pl.ip);
             process_item<T, G, OpLp<T>, false, true>(a, pl, v, gi, lane, true, o, stk, ring);
             break;
         }
@@ -686,8 +701,7 @@ template <typename T, class F> static cudaError_t with_op(T p, F &&f) {
     if (p == T(1)) return f(OpSumAbs<T>{});
     if (p >= cut) return f(OpMaxAbs<T>{});
     OpLp<T> o;
-    o.h = p * T(0.5);
-    o.ip = T(1) / p;
+    o.set(p * T(0.5), T(1) / p);
     return f(o);
 }
 
@@ -701,7 +715,9 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
     const int64_t items = int64_t(1) << pl.dw;
     const int64_t nodes = items - 1;
     Layout L = layout_for(nodes, 1);
-    nrm_status st = nrm_ctx_ensure(c, L.end, nodes);
+    // the tickets of the nodes, and one more counter (the buffer's last) as
+    // the item cursor: every call leaves both at zero
+    nrm_status st = nrm_ctx_ensure(c, L.end, nodes + 1);
     if (st != NRM_OK) return st;
     TreeArgs<T> a{};
     a.x = x;
@@ -713,6 +729,7 @@ static nrm_status run_single(nrm_ctx *c, const T *x, int64_t n, T p, T *out, cud
     a.item_hi = plan_in ? item_hi : items;
     a.total_items = nullptr;
     a.cursor = nullptr;
+    a.item_cursor = c->tickets + (c->tickets_cap - 1);
     a.tickets = c->tickets;
     a.slots = reinterpret_cast<T *>((char *)c->ws + L.slots);
     a.levels = stack_levels(pl.k, tune_of<T>(c).group_log2);

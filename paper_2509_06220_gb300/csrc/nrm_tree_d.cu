@@ -77,6 +77,9 @@ nrm_status na_setup(int dev, NaDevice **out) {
         if (e != cudaSuccess) return NRM_ECUDA;
         int occ = 0;
         const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB, MAXL);
+        e = cudaFuncSetAttribute(tree_kernel<double, NA_G, OpHypot<double>>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return NRM_ECUDA;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tree_kernel<double, NA_G, OpHypot<double>>,
                                                           NA_WPB * 32, smem);
         if (e != cudaSuccess) return NRM_ECUDA;
@@ -135,6 +138,11 @@ extern "C" nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, vo
     const size_t smem = tree_smem_bytes<NA_G, OpHypot<double>>(NA_WPB, MAXL);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((items + NA_WPB - 1) / NA_WPB,
                                                                   (int64_t)d->sms * d->occ));
+    // the kernel's dynamic shared memory limit is a per-function attribute
+    // that other entry points set for their own launches (possibly lower)
+    if (cudaFuncSetAttribute(tree_kernel<double, NA_G, OpHypot<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return NRM_ECUDA;
     tree_kernel<double, NA_G, OpHypot<double>><<<(unsigned)blocks, NA_WPB * 32, smem, s>>>(a, OpHypot<double>{});
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }

@@ -700,6 +700,59 @@ def test_pow_parity(nrm, dt):
     assert f(code, None, None, None, -1, None) != 0
 
 
+def _powr_operands(n, seed):
+    """Operands of the restricted binary64 pow of v1_lp (1 < p <= 2^17) in
+    its two domains: Q in [0, 1) with y = p/2 in (1/2, 2^16] and Z in [1, 2]
+    with y = 1/p in [2^-17, 1): plain draws, x next to 1 on both sides, x at
+    2 and at powers of two, x around 2^-60 and results around the flush
+    limit 2^-28, y at the ends of its ranges."""
+    rng = np.random.default_rng(seed)
+    k = n // 8
+    p = np.exp(rng.uniform(np.log(1.0 + 1e-12), np.log(2.0 ** 17), 8 * k))
+    half = rng.random(8 * k) < 0.5
+    p[half] = rng.choice([1.0 + 2.0 ** -40, 1.5, np.sqrt(2.0), np.e, np.pi, 3.0, 7.5, 64.0], half.sum())
+    p[p == 2.0] = 3.0
+    h, ip = p * 0.5, 1.0 / p
+    xs, ys = [], []
+    xs.append(rng.random(k) ** rng.choice([1, 2, 5, 20], k)); ys.append(h[:k])
+    xs.append(1.0 + rng.random(k)); ys.append(ip[k:2 * k])
+    xs.append(1.0 - rng.random(k) * 2.0 ** -rng.integers(1, 53, k)); ys.append(h[2 * k:3 * k])
+    xs.append(1.0 + rng.random(k) * 2.0 ** -rng.integers(1, 53, k)); ys.append(ip[3 * k:4 * k])
+    xs.append(2.0 ** rng.uniform(-61.5, -58.5, k)); ys.append(rng.uniform(0.5, 0.51, k))
+    # results around 2^-28: y log2 x in [-29, -27]
+    yy = h[5 * k:6 * k]
+    xs.append(2.0 ** (-rng.uniform(27.0, 29.0, k) / yy)); ys.append(yy)
+    xs.append(np.concatenate([np.full(k // 2, 2.0), 2.0 ** -rng.integers(1, 60, k - k // 2).astype(np.float64)]))
+    ys.append(np.concatenate([ip[6 * k:6 * k + k // 2], rng.choice([0.5, 0.75, 1.5, 3.0, 3.75, 4.0], k - k // 2)]))
+    rest = n - 7 * k
+    xs.append(rng.random(rest)); ys.append(np.where(rng.random(rest) < 0.5, 2.0 ** 16, 0.5 + 2.0 ** -52))
+    x, y = np.concatenate(xs), np.concatenate(ys)
+    x[:4] = [0.0, 1.0, 2.0, 5e-324]
+    y[:4] = [1.5, 1.5, 2.0 ** -17, 0.75]
+    return x, y
+
+
+def test_powr_parity(nrm):
+    """The device pow of v1_lp for 1 < p <= 2^17 equals the oracle's
+    or_powr_d bit for bit on 2^20 operand pairs of its two domains."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_powr
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    x, y = _powr_operands(1 << 20, seed=79)
+    xd, yd = dev(x), dev(y)
+    out = torch.empty_like(xd)
+    assert f(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+             x.size, None) == 0
+    got = out.cpu().numpy()
+    want = oracle.powr_arr(x, y)
+    bad = got.view(np.uint64) != want.view(np.uint64)
+    assert not bad.any(), (x[bad][:4], y[bad][:4], got[bad][:4], want[bad][:4])
+    assert (want == 0).sum() > 10000 and (want != 0).sum() > 600000
+    assert f(None, None, None, -1, None) != 0
+
+
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 @pytest.mark.parametrize("p", [0.5, 1.5, 3.0, 7.5, math.pi, 2.0 ** 40])
 def test_lp_combine_parity(nrm, dt, p):

@@ -544,8 +544,19 @@ def test_kernel_pow_tables_match_the_definitions():
     with mpmath.workprec(400):
         iln2 = int(mpmath.floor(mpmath.mpf(2) ** 127 / mpmath.log(2) + mpmath.mpf("0.5")))
         ln2 = int(mpmath.floor(mpmath.log(2) * mpmath.mpf(2) ** 64 + mpmath.mpf("0.5")))
-    const = lambda name: int(re.search(r"%s = 0x([0-9a-f]+)ull" % name, src).group(1), 16)
+    const = lambda name: int(re.search(r"%s = 0x([0-9a-f]+)u" % name, src).group(1), 16)
     assert (const("kPowILN2_HI") << 64 | const("kPowILN2_LO")) == iln2 and const("kPowLN2") == ln2
+    # the restricted pow of v1_lp (1 < p <= 2^17): T1 in Q96 and the series constants
+    with mpmath.workprec(400):
+        two, l2 = mpmath.mpf(2), mpmath.log(2)
+        rn = lambda v: int(mpmath.floor(v + mpmath.mpf("0.5")))
+        T1q = [rn(mpmath.log(mpmath.mpf(512 if j < 128 else 256) / R1[j], 2) * two ** 96) for j in range(256)]
+        D = [rn(two ** 95 / l2), rn(two ** 63 / l2), rn(two ** 64 / (3 * l2)), rn(two ** 32 / (4 * l2)),
+             rn(two ** 32 / (5 * l2))]
+    t1q = block("kPowT1Q96[256][2]")
+    assert [_s128(t1q[2 * j], t1q[2 * j + 1]) for j in range(256)] == T1q
+    assert (const("kPrD1H") << 32 | const("kPrD1L")) == D[0]
+    assert [const("kPrD2"), const("kPrD3"), const("kPrD4"), const("kPrD5")] == D[1:]
 
 
 def _bits_d(v):

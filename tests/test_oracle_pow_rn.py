@@ -190,6 +190,133 @@ def test_pow_s_nearly_correctly_rounded_on_lp_domains():
     assert worst > 0.45
 
 
+def _powr_domain(n, seed):
+    """Operands of or_powr_d, the binary64 pow of v1_lp for 1 < p <= 2^17:
+    S = pow(Q, p/2) with Q in [0, 1) and C = pow(Z, 1/p) with Z in [1, 2],
+    p/2 and 1/p rounded as the tree rounds them; p from the paper's Table 4
+    values above 1, the benchmark's, the ends of the range and random ones;
+    x drawn plainly, next to 1 on both sides, and with results near the
+    flush limit 2^-28."""
+    r = random.Random(seed)
+    ps = [1.0 + 2.0 ** -40, 1.5, math.sqrt(2), math.e, math.pi, 3.0, 7.5, 64.0, 1000.0, 2.0 ** 17]
+    xs, ys = [], []
+    while len(xs) < n:
+        p = r.choice(ps) if r.random() < 0.5 else math.exp(r.uniform(0.0, 17 * math.log(2)))
+        if p == 2.0 or p <= 1.0:
+            continue
+        h, ip = p * 0.5, 1.0 / p
+        kind = len(xs) % 6
+        if kind == 0:
+            x, y = r.random() ** r.choice([1, 2, 5, 20, 60]), h
+        elif kind == 1:
+            x, y = 1.0 + r.random(), ip
+        elif kind == 2:
+            x, y = 1.0 - r.random() * 2.0 ** -r.randint(1, 52), h
+        elif kind == 3:
+            x, y = 1.0 + r.random() * 2.0 ** -r.randint(1, 52), ip
+        elif kind == 4:
+            x, y = 2.0 ** (-r.uniform(26.0, 30.0) / h), h
+        else:
+            x, y = r.uniform(0.0, 1.0) ** r.uniform(0, 60), h
+        if x < 0 or x > 2 or x == 1.0:
+            continue
+        xs.append(x)
+        ys.append(y)
+    return np.array(xs), np.array(ys)
+
+
+def test_powr_d_correctly_rounded_on_lp_domains():
+    """1.2e5 operand pairs of or_powr_d: RN(x^y) bit for bit wherever x^y
+    is more than 2^-8 ulp from a rounding midpoint, within 0.5 + 2^-8 ulp
+    everywhere, for results from 2^-28 up; below 2^-28 (down to 2^-28 less
+    2^-8 ulp, which may round either way) the result is +0 or below 2^-27,
+    so that RN(1 + S^2) = 1 as for the exact S.  Where it is not flushed it
+    equals or_pow_d away from the midpoints (both are RN there)."""
+    x, y = _powr_domain(120000, seed=53)
+    v = oracle.powr_arr(x, y)
+    g = oracle.pow_arr(x, y)
+    lim = mpmath.ldexp(1, -28)
+    checked = decided = flushed = 0
+    worst = 0.0
+    with mpmath.workprec(PREC):
+        for i in range(x.size):
+            xi, yi, vi = float(x[i]), float(y[i]), float(v[i])
+            ex = mpmath.mpf(xi) ** mpmath.mpf(yi)
+            if ex < lim:
+                assert vi < 2.0 ** -27 and 1.0 + vi * vi == 1.0, (xi.hex(), yi.hex(), vi)
+                flushed += vi == 0.0
+                continue
+            want, dist, q = _rn(ex, 52, -1022)
+            err = _ulp_err(vi, ex, q)
+            worst = max(worst, err)
+            assert err <= 0.5 + 2.0 ** -8, (xi.hex(), yi.hex(), err)
+            checked += 1
+            if dist > 2.0 ** -8:
+                decided += 1
+                assert vi == want, ("not RN(x^y)", xi.hex(), yi.hex(), vi, want, dist)
+                assert float(g[i]) == want
+    assert checked > 80000 and decided > 0.98 * checked and flushed > 10000
+    assert worst > 0.45
+
+
+def test_powr_d_exact_cases():
+    """pow(0, y) = 0 and pow(1, y) = 1; x = 2^a with a y an integer gives
+    2^(ay) exactly (u = 0 in the reductions, no series term, t an
+    integer); pow(2, y) for y = 2^-k."""
+    xs = [0.0, 0.0, 1.0, 1.0, 0.25, 0.5, 0.5, 2.0 ** -10, 2.0, 2.0, 0.125, 2.0 ** -28, 2.0 ** -7]
+    ys = [0.75, 2.0 ** 16, 0.75, 2.0 ** -17, 1.5, 3.0, 28.0, 2.5, 1.0, 0.5, 9.0, 1.0, 4.0]
+    want = [0.0, 0.0, 1.0, 1.0, 0.125, 0.125, 2.0 ** -28, 2.0 ** -25, 2.0, math.sqrt(2.0), 2.0 ** -27,
+            2.0 ** -28, 2.0 ** -28]
+    got = oracle.powr_arr(np.array(xs), np.array(ys))
+    assert list(got) == want
+    # flushed: 2^-29 and below, and x under 2^-60 for any y >= 1/2
+    got = oracle.powr_arr(np.array([0.5, 2.0 ** -61, 5e-324, 0.25]), np.array([29.0, 0.5, 0.5, 14.5]))
+    assert list(got) == [0.0, 0.0, 0.0, 0.0]
+
+
+def test_powr_table_matches_its_definition():
+    """or_powr_d's Q96 logarithm table, built by the oracle from binary128
+    log2, equals RN(log2(2^9 / r1_j) 2^96) (j < 128) or RN(log2(2^8 / r1_j)
+    2^96) at 400 bits, entry by entry; its constants D1..D5 are 2^95/ln 2,
+    2^63/ln 2, 2^64/(3 ln 2), 2^32/(4 ln 2), 2^32/(5 ln 2) rounded to
+    nearest."""
+    import re
+    from fractions import Fraction
+    with mpmath.workprec(400):
+        R1 = [512] + [int(Fraction(1 << 18, 513 + 2 * j) + Fraction(1, 2)) for j in range(1, 256)]
+        rn = lambda v: int(mpmath.floor(v + mpmath.mpf("0.5")))
+        T1q = [rn(mpmath.log(mpmath.mpf(512 if j < 128 else 256) / R1[j], 2) * mpmath.mpf(2) ** 96)
+               for j in range(256)]
+        ln2 = mpmath.log(2)
+        two = mpmath.mpf(2)
+        D = [rn(two ** 95 / ln2), rn(two ** 63 / ln2), rn(two ** 64 / (3 * ln2)), rn(two ** 32 / (4 * ln2)),
+             rn(two ** 32 / (5 * ln2))]
+    assert oracle.powr_table() == T1q
+    assert T1q[0] == 0 and T1q[255] == 0
+    src = open(oracle._build.SRC).read()
+    macro = lambda name: int(re.search(r"#define %s 0x([0-9a-f]+)ull" % name, src).group(1), 16)
+    assert (macro("PR_D1H") << 32 | macro("PR_D1L")) == D[0]
+    assert [macro("PR_D2"), macro("PR_D3"), macro("PR_D4"), macro("PR_D5")] == D[1:]
+
+
+def test_powr_pin_catches_a_planted_error():
+    """A one-ulp slip on 1 case in 64 of or_powr_d's results fails the
+    bitwise check, as for the general pow."""
+    x, y = _powr_domain(4000, seed=59)
+    v = oracle.powr_arr(x, y)
+    idx = [i for i in range(0, v.size, 64) if v[i] != 0.0]
+    bad = v.copy()
+    bad[idx] = np.nextafter(v[idx], np.inf)
+    caught = 0
+    with mpmath.workprec(PREC):
+        for i in idx:
+            ex = mpmath.mpf(float(x[i])) ** mpmath.mpf(float(y[i]))
+            want, dist, _ = _rn(ex, 52, -1022)
+            if dist > 2.0 ** -8 and float(bad[i]) != want:
+                caught += 1
+    assert caught > 0.5 * len(idx)
+
+
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_pin_catches_a_planted_error(dt):
     """The pin is sharp enough to see a one-ulp slip: the oracle's pow with
