@@ -107,20 +107,38 @@ extern "C" nrm_status nrm_gen_ragged(nrm_dtype dtype, void *x, int64_t x_len, co
 uint64_t nrm_gen_key(uint64_t seed, uint64_t vec) { return key_of(seed, vec); }
 
 namespace {
+// Tiles of GEN_TILE consecutive elements of the concatenated segments: the
+// segment of a tile's first element is found once per tile (the same
+// binary search in every thread of the block, uniform loads), and each
+// thread then walks its elements of the tile in order, stepping to the next
+// segment where one ends (segments are long: a tile rarely crosses one).
+constexpr int GEN_TILE = 4096;
 __global__ void gen_segments_kernel(const NrmGenSeg *segs, const int64_t *cum, int64_t count, int64_t total,
                                     void *arena) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = 0, hi = count; // last segment with cum <= e
+    for (int64_t t0 = (int64_t)blockIdx.x * GEN_TILE; t0 < total; t0 += (int64_t)gridDim.x * GEN_TILE) {
+        int64_t lo = 0, hi = count; // last segment with cum <= t0
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
-            if (cum[mid] <= e) lo = mid;
+            if (__ldg(cum + mid) <= t0) lo = mid;
             else hi = mid;
         }
-        const NrmGenSeg sg = segs[lo];
-        const int64_t i = e - cum[lo];
-        const uint64_t u = draw(sg.key, (uint64_t)i);
-        if (sg.dtype == NRM_F64) ((double *)arena)[sg.start + i] = elem_d(u, sg.emin, (uint64_t)sg.span);
-        else ((float *)arena)[sg.start + i] = elem_s(u, sg.emin, (uint64_t)sg.span);
+        const int64_t t1 = t0 + GEN_TILE < total ? t0 + GEN_TILE : total;
+        int64_t seg = lo;
+        int64_t base = __ldg(cum + seg);
+        int64_t end = seg + 1 < count ? __ldg(cum + seg + 1) : total;
+        NrmGenSeg sg = segs[seg];
+        for (int64_t e = t0 + threadIdx.x; e < t1; e += blockDim.x) {
+            while (e >= end) {
+                ++seg;
+                base = end;
+                end = seg + 1 < count ? __ldg(cum + seg + 1) : total;
+                sg = segs[seg];
+            }
+            const int64_t i = e - base;
+            const uint64_t u = draw(sg.key, (uint64_t)i);
+            if (sg.dtype == NRM_F64) ((double *)arena)[sg.start + i] = elem_d(u, sg.emin, (uint64_t)sg.span);
+            else ((float *)arena)[sg.start + i] = elem_s(u, sg.emin, (uint64_t)sg.span);
+        }
     }
 }
 } // namespace
@@ -128,7 +146,7 @@ __global__ void gen_segments_kernel(const NrmGenSeg *segs, const int64_t *cum, i
 nrm_status nrm_gen_segments(const NrmGenSeg *segs_dev, const int64_t *cum_dev, int64_t count, int64_t total,
                             void *arena, cudaStream_t s) {
     if (count <= 0 || total <= 0) return NRM_OK;
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 32);
+    const int64_t blocks = std::min<int64_t>((total + GEN_TILE - 1) / GEN_TILE, 152 * 8);
     gen_segments_kernel<<<(unsigned)blocks, 256, 0, s>>>(segs_dev, cum_dev, count, total, arena);
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }
