@@ -58,9 +58,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # summaries are committed beside the code); set the flag to False whenever
 # the binary64 tree kernel changes, and re-capture.
 NCU_VALID = True
-TRAFFIC_D_2E28 = 2149.753344e6 + 29.499904e6  # DNRMF: DRAM read + write of one launch at n = 2^28
-TRAFFIC_S_2E28 = 1075.622912e6 + 8.598784e6  # SNRMF: the same
-INST_PER_ELEM_D = 174.1  # DNRMF: smsp__inst_executed.sum x 32 / n at n = 2^26 (thread-instructions per element)
+TRAFFIC_D_2E28 = 2194.844928e6 + 109.01248e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1076.181504e6 + 36.761088e6  # SNRMF: the same
+INST_PER_ELEM_D = 166.6  # DNRMF: smsp__inst_executed.sum x 32 / n at n = 2^26 (thread-instructions per element)
+ALU_PER_ELEM_D = 88.87   # DNRMF: sm__inst_executed_pipe_alu.sum x 32 / n at n = 2^26 (the ALU pipe: 64 lanes an SM)
+ALU_PER_SM_CLK = 64
 FP64_PER_COMBINE_D = 2   # DNRMF: one DFMA (S = 1 + Q^2) and one DMUL (h = M s) per v1_hypot
 ISSUE_PER_SM_CLK = 4 * 32  # thread-instructions an SM issues per clock (4 schedulers x 1 warp-instruction)
 
@@ -222,13 +224,15 @@ def event_ms(torch, fn, reps):
 
 def roofline_d(ms, n, fp64_rate, fp64_src, hbm_gbs, hbm_src, sms, sm_mhz):
     """The roofline of one DNRMF launch of n elements taking ms: the slowest
-    of its floors (HBM bytes, FP64 instructions, issued instructions); the
-    fraction is that floor's time over the launch time."""
+    of its floors (HBM bytes, FP64 instructions, issued instructions, ALU-pipe
+    instructions); the fraction is that floor's time over the launch time."""
     floors = {"hbm": n * 8 / (hbm_gbs * 1e9) * 1e3,
               "fp64_pipe": FP64_PER_COMBINE_D * (n - 1) / fp64_rate * 1e3,
-              "issue": INST_PER_ELEM_D * n / (sms * ISSUE_PER_SM_CLK * sm_mhz * 1e6) * 1e3}
+              "issue": INST_PER_ELEM_D * n / (sms * ISSUE_PER_SM_CLK * sm_mhz * 1e6) * 1e3,
+              "alu_pipe": ALU_PER_ELEM_D * n / (sms * ALU_PER_SM_CLK * sm_mhz * 1e6) * 1e3}
     if not NCU_VALID:
         floors.pop("issue")
+        floors.pop("alu_pipe")
     bind = max(floors, key=floors.get)
     if bind == "hbm":
         r = {"bound": "hbm", "achieved": n * 8 / (ms * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
@@ -236,11 +240,16 @@ def roofline_d(ms, n, fp64_rate, fp64_src, hbm_gbs, hbm_src, sms, sm_mhz):
     elif bind == "fp64_pipe":
         r = {"bound": "alu", "achieved": FP64_PER_COMBINE_D * (n - 1) / (ms * 1e-3) / 1e9, "peak": fp64_rate / 1e9,
              "unit": "G FP64 instructions/s (DFMA + DMUL, one each per v1_hypot)", "peak_source": fp64_src}
-    else:
+    elif bind == "issue":
         r = {"bound": "alu", "achieved": INST_PER_ELEM_D * n / (ms * 1e-3) / 1e9,
              "peak": sms * ISSUE_PER_SM_CLK * sm_mhz / 1e3,
              "unit": "G thread-instructions/s issued (%.1f per element, ncu)" % INST_PER_ELEM_D,
              "peak_source": "%d SMs x 4 warp-instructions per clock x %.0f MHz (the maximum SM clock)" % (sms, sm_mhz)}
+    else:
+        r = {"bound": "alu", "achieved": ALU_PER_ELEM_D * n / (ms * 1e-3) / 1e9,
+             "peak": sms * ALU_PER_SM_CLK * sm_mhz / 1e3,
+             "unit": "G thread-instructions/s on the ALU pipe (%.2f per element, ncu)" % ALU_PER_ELEM_D,
+             "peak_source": "%d SMs x 64 ALU lanes x %.0f MHz (the maximum SM clock)" % (sms, sm_mhz)}
     r["frac"] = r["achieved"] / r["peak"]
     r["binding_floor"] = bind
     r["floors_ms"] = floors
@@ -412,6 +421,11 @@ def _serve_summary(nrm, tr, lat, rep, window_s=10.0):
         out["p99_first_%gs_ms" % window_s] = p_first
         out["p99_last_%gs_ms" % window_s] = p_last
         out["p99_bounded"] = bool(p_last <= 1.5 * p_first)
+        # p99 of every window of arrivals, and the time of the slowest request
+        edges = np.arange(0.0, T + window_s, window_s)
+        out["p99_by_window_ms"] = [round(float(np.percentile(lat[(arr >= a) & (arr < a + window_s)], 99)), 3)
+                                   for a in edges[:-1] if ((arr >= a) & (arr < a + window_s)).any()]
+        out["max_latency_arrival_s"] = float(arr[int(np.argmax(lat))])
     return out
 
 
@@ -460,6 +474,40 @@ def time_serving(nrm, seconds, rate, baseline_seconds, saturation):
     return res
 
 
+def run_capture(args):
+    """The launches of one part of the benchmark alone, for ncu launch lists
+    (prints one JSON line of its own timings; not a benchmark line)."""
+    import numpy as np
+    import torch
+
+    import paper_2509_06220_gb300 as nrm
+    from paper_2509_06220_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    res = {"capture": args.capture}
+    if args.capture == "batch":
+        L = inputs.ragged_lengths(4096, seed=0)
+        off = np.zeros(4097, np.int64)
+        np.cumsum(L, out=off[1:])
+        offd = torch.from_numpy(off).to(dev)
+        for name, td, code in (("f64", torch.float64, nrm.NRM_F64), ("f32", torch.float32, nrm.NRM_F32)):
+            x = nrm.nrm_gen_ragged(offd, seed=0, dtype=td)
+            bctx = nrm.Context(0)
+            tuned = bctx.autotune(code, L)
+            g = nrm.nrm_batch_graph(x, offd, ctx=bctx)
+            res[name] = {"tuning": tuned, "ms_per_batch": event_ms(torch, g.launch, max(args.steps, 1))}
+            g.close()
+            bctx.close()
+    else:
+        tr = nrm.serving_trace(args.serve_rate, args.serve_seconds, seed=0)
+        back = nrm.trace_records(tr).copy()
+        back["arrival_s"] = 0.0
+        bt = (nrm.Request * len(back)).from_buffer_copy(back.tobytes())
+        _, _, rep = _replay(nrm, bt, 4, 256)
+        res["serve"] = {"requests": rep["completed"], "norms_per_s": rep["completed"] / max(rep["wall_s"], 1e-9),
+                        "elements_per_s": rep["elements_per_s"]}
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,7 +530,14 @@ def main():
     ap.add_argument("--p", type=float, default=2.0,
                     help="xNRMP with this p instead of xNRMF (profiling captures of the p-norm kernels; "
                          "the e2e, batch, serving and oracle legs and the v1_hypot roofline are left out)")
+    ap.add_argument("--capture", default="", choices=["", "batch", "serve"],
+                    help="profiling captures: 'batch' replays only the autotuned config-2 batch graphs (--steps "
+                         "replays per type), 'serve' serves only a backlog of the config-4 trace's first "
+                         "--serve-seconds seconds, all arriving at once")
     args = ap.parse_args()
+    if args.capture:
+        run_capture(args)
+        return
     if args.p != 2.0:
         args.no_e2e = args.no_cpu_baseline = args.no_batch = True
         args.serve_seconds = 0

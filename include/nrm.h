@@ -428,7 +428,9 @@ void nrm_test_inject_alloc_failures(int count);
  * pointer); example (device, 4 doubles) receives the first differing
  * x, y and both results.  mode 8..14: family mode - 8 with the branch-free
  * form of checked groups, on the pairs inside its range [2^-500, 2^502)
- * (others skipped).  NRM_EINVAL for another mode. */
+ * (others skipped); mode 16..22: the same with the paired branch-free form
+ * (two operand pairs at once, as the tree kernels combine two lanes),
+ * against the FP64 form of each pair.  NRM_EINVAL for another mode. */
 nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad, double *example,
                                 void *stream);
 

@@ -593,17 +593,37 @@ __device__ __forceinline__ void k1d_pair(uint64_t seed, int64_t i, int mode, dou
 
 // mode 0..6: k1_exact on family `mode`; mode 8..14: k1_exact_fast on family
 // mode - 8, for the pairs inside its range [2^-500, 2^502) (others skipped)
+__device__ __forceinline__ bool in_fast_range(double x, double y) {
+    const uint32_t hx = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32) & 0x7fffffffu;
+    const uint32_t hy = (uint32_t)((uint64_t)__double_as_longlong(y) >> 32) & 0x7fffffffu;
+    const uint32_t lo = (uint32_t)(1023 - 500) << 20, hi = (uint32_t)(1023 + 502) << 20;
+    return hx >= lo && hx < hi && hy >= lo && hy < hi;
+}
 __global__ void k1d_compare_kernel(uint64_t seed, int64_t n, int mode, unsigned long long *bad, double *example) {
+    const bool pair = mode >= 16;
     const bool fast = mode >= 8;
     const int fam = mode & 7;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double x, y;
         k1d_pair(seed, i, fam, x, y);
-        if (fast) {
-            const uint32_t hx = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32) & 0x7fffffffu;
-            const uint32_t hy = (uint32_t)((uint64_t)__double_as_longlong(y) >> 32) & 0x7fffffffu;
-            const uint32_t lo = (uint32_t)(1023 - 500) << 20, hi = (uint32_t)(1023 + 502) << 20;
-            if (hx < lo || hx >= hi || hy < lo || hy >= hi) continue;
+        if (fast && !in_fast_range(x, y)) continue;
+        if (pair) {
+            // the paired form on pair i and a second pair of the family,
+            // against the FP64 form of each
+            double x2, y2, a, a2;
+            k1d_pair(seed ^ 0x5bd1e9955bd1e995ull, i, fam, x2, y2);
+            if (!in_fast_range(x2, y2)) continue;
+            k1_exact_fast2(x, y, x2, y2, a, a2);
+            const double b = k1(x, y), b2 = k1(x2, y2);
+            const bool same = __double_as_longlong(a) == __double_as_longlong(b) &&
+                              __double_as_longlong(a2) == __double_as_longlong(b2);
+            if (!same && atomicAdd(bad, 1ull) == 0ull) {
+                example[0] = x;
+                example[1] = y;
+                example[2] = a;
+                example[3] = b;
+            }
+            continue;
         }
         const double a = fast ? k1_exact_fast(x, y) : k1_exact(x, y), b = k1(x, y);
         const bool same = (__double_as_longlong(a) == __double_as_longlong(b)) || (isnan(a) && isnan(b));
@@ -816,7 +836,7 @@ extern "C" nrm_status nrm_test_k2d_compare(uint64_t seed, int64_t n, int32_t mod
 
 extern "C" nrm_status nrm_test_k1d_compare(uint64_t seed, int64_t n, int32_t mode, unsigned long long *bad,
                                            double *example, void *stream) {
-    if (n < 0 || !bad || !example || mode < 0 || mode > 14 || mode == 7) return NRM_EINVAL;
+    if (n < 0 || !bad || !example || mode < 0 || mode > 22 || (mode & 7) == 7) return NRM_EINVAL;
     k1d_compare_kernel<<<152 * 16, 256, 0, (cudaStream_t)stream>>>(seed, n, mode, bad, example);
     return cudaGetLastError() == cudaSuccess ? NRM_OK : NRM_ECUDA;
 }

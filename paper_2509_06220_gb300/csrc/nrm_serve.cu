@@ -27,7 +27,6 @@
 #include <map>
 #include <mutex>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "../../include/nrm.h"
@@ -127,7 +126,10 @@ struct nrm_srv {
     std::mutex mu;
     std::condition_variable cv_done;
     std::deque<Req *> pending, admitted;
-    std::unordered_map<uint64_t, Req *> reqs;
+    // every request by id (ids are consecutive from 0); a deque grows without
+    // the rehash pauses of a hash map, which stalled the loop for ~0.1 s once
+    // a trace reached 1.5 M requests
+    std::deque<Req *> reqs;
     uint64_t next_id = 0;
     std::thread worker;
     std::atomic<bool> stop{false};
@@ -137,7 +139,7 @@ struct nrm_srv {
     double host_launch_s = 0, host_retire_s = 0, gpu_step_s = 0; // worker-written, read under mu
     std::atomic<int64_t> steps{0}, launches{0}, elements{0}, peak_bytes{0}; // worker-written
     int64_t max_queue = 0;
-    std::vector<double> lat_ms;
+    std::deque<double> lat_ms;
     clk::time_point t_first, t_last;
     bool any = false;
     nrm_status fatal = NRM_OK;
@@ -431,7 +433,7 @@ extern "C" nrm_status nrm_srv_destroy(nrm_srv *s) {
         if (ln.ctx) nrm_destroy(ln.ctx);
     }
     if (s->arena_ptr) cudaFree(s->arena_ptr);
-    for (auto &kv : s->reqs) delete kv.second;
+    for (Req *q : s->reqs) delete q;
     delete s;
     return NRM_OK;
 }
@@ -453,7 +455,7 @@ static nrm_status submit_at(nrm_srv *s, const nrm_request *r, clk::time_point t_
     q->id = s->next_id++;
     q->r = *r;
     q->t_arrival = t_arrival;
-    s->reqs[q->id] = q;
+    s->reqs.push_back(q); // at index q->id
     s->pending.push_back(q);
     if (id) *id = q->id;
     return NRM_OK;
@@ -466,12 +468,12 @@ extern "C" nrm_status nrm_srv_submit(nrm_srv *s, const nrm_request *r, uint64_t 
 extern "C" nrm_status nrm_srv_poll(nrm_srv *s, uint64_t id, double *norm, int32_t *status, int32_t *done) {
     if (!s || !done) return NRM_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(id);
-    if (it == s->reqs.end()) return NRM_EINVAL;
-    *done = it->second->done ? 1 : 0;
-    if (it->second->done) {
-        if (norm) *norm = it->second->result;
-        if (status) *status = it->second->status;
+    if (id >= (uint64_t)s->reqs.size()) return NRM_EINVAL;
+    const Req *q = s->reqs[(size_t)id];
+    *done = q->done ? 1 : 0;
+    if (q->done) {
+        if (norm) *norm = q->result;
+        if (status) *status = q->status;
     }
     return NRM_OK;
 }
@@ -502,7 +504,7 @@ extern "C" nrm_status nrm_srv_report_get(nrm_srv *s, nrm_srv_report *rep) {
     rep->host_launch_s = s->host_launch_s;
     rep->host_retire_s = s->host_retire_s;
     rep->gpu_step_s = s->gpu_step_s;
-    std::vector<double> v = s->lat_ms;
+    std::vector<double> v(s->lat_ms.begin(), s->lat_ms.end());
     if (!v.empty()) {
         std::sort(v.begin(), v.end());
         auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5))]; };
@@ -541,7 +543,7 @@ extern "C" nrm_status nrm_srv_replay(nrm_srv *s, const nrm_request *reqs, int64_
         std::lock_guard<std::mutex> lk(s->mu);
         for (int64_t i = 0; i < count; ++i) {
             const uint64_t id = ids[(size_t)i];
-            Req *q = id == UINT64_MAX ? nullptr : s->reqs[id];
+            Req *q = id == UINT64_MAX ? nullptr : s->reqs[(size_t)id];
             if (norms) norms[i] = q ? q->result : __builtin_nan("");
             if (latency_ms) latency_ms[i] = q ? secs(q->t_arrival, q->t_done) * 1e3 : -1.0;
         }

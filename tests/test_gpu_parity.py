@@ -555,6 +555,27 @@ def test_k1_fast_matches_fp64(nrm, mode):
     assert f(1, 1, 7, ctypes.c_void_p(bad.data_ptr()), ctypes.c_void_p(ex.data_ptr()), None) == nrm.NRM_EINVAL
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 5, 6])
+def test_k1_fast_pair_matches_fp64(nrm, mode):
+    """The paired checked-group binary64 v1_hypot (two operand pairs at
+    once, their FP32 estimates in paired FFMA2 / FMUL2 / FADD2 instructions)
+    equals the FP64 v1_hypot of Listing 2 on both pairs, bit for bit, on
+    2^29 generated pairs of pairs per family inside its range."""
+    import ctypes
+    L = nrm.load()
+    f = L.nrm_test_k1d_compare
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    bad = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ex = torch.zeros(4, dtype=torch.float64, device=DEV)
+    for rep in range(2):
+        assert f(97531 + 1000 * mode + rep, 1 << 28, 16 + mode, ctypes.c_void_p(bad.data_ptr()),
+                 ctypes.c_void_p(ex.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0, ex.cpu().numpy()
+    assert f(1, 1, 23, ctypes.c_void_p(bad.data_ptr()), ctypes.c_void_p(ex.data_ptr()), None) == nrm.NRM_EINVAL
+
+
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_autotune_keeps_bits(nrm, dt):
     """The autotuner picks a valid tuning; results before and after are
