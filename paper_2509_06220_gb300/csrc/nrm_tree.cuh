@@ -457,33 +457,6 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         items = int64_t(1) << pl.dw;
         nodes = items - 1;
     };
-    // totals; segments may overlap, so their nodes are not bounded by x_len:
-    // deeper work items need fewer tickets (the tree is unchanged)
-    int64_t total_items, total_nodes;
-    for (;;) {
-        int64_t ti = 0, tn = 0;
-        for (int64_t r = 0; r < rounds; ++r) {
-            const int64_t v = r * 1024 + tid;
-            int64_t it = 0, nd = 0;
-            if (v < B) {
-                VecPlan pl;
-                int32_t st;
-                plan_of(v, pl, it, nd, st);
-            }
-            int64_t si, sn;
-            block_scan_1024(it, s_warp, &si);
-            block_scan_1024(nd, s_warp, &sn);
-            ti += si;
-            tn += sn;
-        }
-        total_items = ti;
-        total_nodes = tn;
-        if (total_nodes <= node_cap || kk >= kmax) break;
-        ++kk;
-    }
-    // If even the deepest work items need more ticket nodes than the
-    // workspace holds, no vector is computed and all report NRM_ENOMEM.
-    const bool overflow = total_nodes > node_cap;
     // Work order: the persistent grid takes work items in index order, so
     // the vectors are numbered longest first: a counting sort on n in
     // quarter-octave classes (floor(log2 n) and its next two bits; the last
@@ -498,8 +471,12 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     constexpr int NB = 4 * NL;       // (combine, length) classes, NB <= 1024
     __shared__ unsigned s_cnt[NB], s_cur[NB];
     __shared__ int64_t s_vbase[NB];
+    // item counts of the plans in plan order (the first PLAN_SMEM of them;
+    // the rest are read back from the plans)
+    constexpr int PLAN_SMEM = 8192;
+    __shared__ int32_t s_items[PLAN_SMEM];
     auto bucket_of = [&](const VecPlan &pl, int64_t items) {
-        if (items == 0 || overflow) return NB - 1;
+        if (items == 0) return NB - 1;
         const int64_t n = pl.n;
         const int lg = 63 - __clzll((long long)n); // n >= 1
         const int cls = lg >= 40 ? 4 * 40 + 3 : 4 * lg + (lg >= 2 ? (int)((n >> (lg - 2)) & 3) : 0);
@@ -508,27 +485,42 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     };
     const int lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u; // lanes below this one
-    for (int q = tid; q < NB; q += 1024) s_cnt[q] = s_cur[q] = 0u;
-    __syncthreads();
-    // statuses, the outputs of empty or bad vectors, and the class counts
-    for (int64_t r = 0; r < rounds; ++r) {
-        const int64_t v = r * 1024 + tid;
-        const bool valid = v < B;
-        int q = NB; // no class
-        if (valid) {
-            VecPlan pl;
-            int64_t it, nd;
-            int32_t st;
-            plan_of(v, pl, it, nd, st);
-            if (overflow && st == NRM_OK) st = NRM_ENOMEM;
-            if (status) status[v] = st;
-            if (st != NRM_OK) out[v] = T(NAN);
-            else if (pl.n == 0) out[v] = T(0);
-            q = bucket_of(pl, it);
+    // One pass: the ticket nodes of all vectors and the class counts.
+    // Segments may overlap, so their nodes are not bounded by x_len: if the
+    // nodes exceed the workspace, deeper work items need fewer of them (the
+    // tree is unchanged), and the pass is repeated at the next depth.
+    int64_t total_nodes;
+    for (;;) {
+        for (int q = tid; q < NB; q += 1024) s_cnt[q] = s_cur[q] = 0u;
+        __syncthreads();
+        int64_t tn = 0;
+        for (int64_t r = 0; r < rounds; ++r) {
+            const int64_t v = r * 1024 + tid;
+            const bool valid = v < B;
+            int64_t it = 0, nd = 0;
+            int q = NB; // no class
+            if (valid) {
+                VecPlan pl;
+                int32_t st;
+                plan_of(v, pl, it, nd, st);
+                q = bucket_of(pl, it);
+            }
+            const unsigned grp = __match_any_sync(FULL, q);
+            if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
+            int64_t sn;
+            block_scan_1024(nd, s_warp, &sn);
+            tn += sn;
         }
-        const unsigned grp = __match_any_sync(FULL, q);
-        if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
+        total_nodes = tn;
+        if (total_nodes <= node_cap || kk >= kmax) break;
+        ++kk;
     }
+    // If even the deepest work items need more ticket nodes than the
+    // workspace holds, no vector is computed and all report NRM_ENOMEM (all
+    // in the last class, without work items).
+    const bool overflow = total_nodes > node_cap;
+    if (overflow)
+        for (int q = tid; q < NB; q += 1024) s_cnt[q] = q == NB - 1 ? (unsigned)B : 0u;
     __syncthreads();
     // first plan index of every class: an exclusive scan over the classes
     {
@@ -538,7 +530,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         if (tid < NB) s_vbase[tid] = incl - c;
         __syncthreads();
     }
-    // the plans, in class order, with their item counts in item_base for now
+    // the plans, in class order, with their item counts in item_base for
+    // now; statuses and the outputs of empty or bad vectors
     int64_t nbase = 0; // ticket nodes of the earlier rounds
     for (int64_t r = 0; r < rounds; ++r) {
         const int64_t v = r * 1024 + tid;
@@ -549,7 +542,13 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         if (valid) {
             int32_t st;
             plan_of(v, pl, it, nd, st);
-            if (overflow) it = 0;
+            if (overflow) {
+                it = 0;
+                if (st == NRM_OK) st = NRM_ENOMEM;
+            }
+            if (status) status[v] = st;
+            if (st != NRM_OK) out[v] = T(NAN);
+            else if (pl.n == 0) out[v] = T(0);
             q = bucket_of(pl, it);
         }
         int64_t sn;
@@ -563,7 +562,9 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
             pl.node_base = nbase + incl - nd;
             pl.out_idx = v;
             pl.item_base = it;
-            store_plan(plans + s_vbase[q] + base + __popc(grp & lt), pl);
+            const int64_t slot = s_vbase[q] + base + __popc(grp & lt);
+            store_plan(plans + slot, pl);
+            if (slot < PLAN_SMEM) s_items[slot] = (int32_t)it;
         }
         nbase += sn;
     }
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     int64_t ibase = 0;
     for (int64_t r = 0; r < rounds; ++r) {
         const int64_t s = r * 1024 + tid;
-        const int64_t c = s < B ? plans[s].item_base : 0;
+        const int64_t c = s < B ? (s < PLAN_SMEM ? (int64_t)s_items[s] : plans[s].item_base) : 0;
         int64_t tot;
         const int64_t incl = block_scan_1024(c, s_warp, &tot);
         if (s < B) {
@@ -581,6 +582,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         }
         ibase += tot;
     }
+    const int64_t total_items = ibase;
     if (tid == 0) {
         totals[0] = overflow ? 0 : total_items;
         totals[1] = total_nodes;
