@@ -775,7 +775,9 @@ def test_powr_parity(nrm):
 
 
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
-@pytest.mark.parametrize("p", [0.5, 1.5, 3.0, 7.5, math.pi, 2.0 ** 40])
+@pytest.mark.parametrize("p", [0.5, 1.5, 3.0, 7.5, math.pi, 2.0 ** 40,
+                               # the ends of the restricted pow's range (1 < p <= 2^17) and just past it
+                               1.0 + 2.0 ** -40, 2.0 ** 17, 2.0 ** 17 * (1.0 + 2.0 ** -50)])
 def test_lp_combine_parity(nrm, dt, p):
     """v1_lp on the device (binary64: integer quotient and pow, FP64 form for
     inf, NaN and subnormal operands) equals the oracle's v1_lp bit for bit on
