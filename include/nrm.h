@@ -354,6 +354,11 @@ nrm_status nrmf_d_noalloc(const double *x, int64_t n, double *out, void *stream)
  */
 nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t *lengths_host, int64_t B, nrm_tuning *best);
 
+/* nrm_autotune without the tuning read-back (best = NULL): the name of the
+ * autotuner in the library's interface sketch.  Same arguments, effects and
+ * errors. */
+nrm_status nrm_tune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t *lengths_host, int64_t B);
+
 /*
  * Continuous-batching server.  Requests (element type, p, length; input
  * copied from the host or generated on the device) are submitted at any

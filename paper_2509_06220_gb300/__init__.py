@@ -106,6 +106,7 @@ def load():
         "nrm_gen_ragged": (st, [i32, vp, i64, vp, i64, u64, i32, i32, vp]),
         "nrm_kernel_launches": (u64, [vp]),
         "nrm_autotune": (st, [vp, i32, vp, i64, ctypes.POINTER(Tuning)]),
+        "nrm_tune": (st, [vp, i32, vp, i64]),
         "nrm_batch_segments": (st, [vp, i32, vp, i64, vp, vp, i64, ctypes.c_double, vp, vp, vp, vp]),
         "nrm_strided": (st, [vp, i32, vp, i64, i64, ctypes.c_double, vp, vp]),
         "nrm_matrix": (st, [vp, i32, vp, i64, i64, i64, ctypes.c_double, vp, vp]),

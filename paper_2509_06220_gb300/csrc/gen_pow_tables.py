@@ -86,12 +86,12 @@ def main():
         out.append("    " + " ".join("%d," % R1[k] for k in range(j, j + 16)))
     out.append("};")
     out.append("// T1_j = RN(log2(2^9 or 2^8 / r1_j) 2^88) as a two's-complement 128-bit {high, low}")
-    out.append("static __device__ const uint64_t kPowT1[256][2] = {")
+    out.append("static __device__ __align__(16) const uint64_t kPowT1[256][2] = {")
     for j in range(0, 256, 2):
         out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (((T1[k] >> 64) & M), T1[k] & M) for k in (j, j + 1)))
     out.append("};")
     out.append("// T2_j2 = RN(-log2(1 - j2 2^-16) 2^96), index j2 + %d, as {high, low}" % J2MAX)
-    out.append("static __device__ const uint64_t kPowT2[%d][2] = {" % (2 * J2MAX + 1))
+    out.append("static __device__ __align__(16) const uint64_t kPowT2[%d][2] = {" % (2 * J2MAX + 1))
     for k in range(0, 2 * J2MAX + 1, 2):
         ks = [k] if k + 1 > 2 * J2MAX else [k, k + 1]
         out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (((T2[i] >> 64) & M), T2[i] & M) for i in ks))
@@ -103,7 +103,7 @@ def main():
     out.append("};")
     T1q, D = powr_tables()
     out.append("// T1q_j = RN(log2(2^9 or 2^8 / r1_j) 2^96) as a two's-complement 128-bit {high, low}")
-    out.append("static __device__ const uint64_t kPowT1Q96[256][2] = {")
+    out.append("static __device__ __align__(16) const uint64_t kPowT1Q96[256][2] = {")
     for j in range(0, 256, 2):
         out.append("    " + " ".join("{0x%016xull, 0x%016xull}," % (((T1q[k] >> 64) & M), T1q[k] & M) for k in (j, j + 1)))
     out.append("};")

@@ -276,3 +276,7 @@ extern "C" nrm_status nrm_autotune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t 
     if (best_out) *best_out = ctx->tune[dtype];
     return st;
 }
+
+extern "C" nrm_status nrm_tune(nrm_ctx *ctx, nrm_dtype dtype, const int64_t *lengths_host, int64_t B) {
+    return nrm_autotune(ctx, dtype, lengths_host, B, nullptr);
+}

@@ -595,6 +595,14 @@ def test_autotune_keeps_bits(nrm, dt):
         ctx.autotune(code, np.diff(off))
         out, _ = nrm.nrm_batch(dev(xb), dev(off), ctx=ctx)
         assert bits_equal(out.cpu().numpy(), oracle.nrm_batch(xb, off))
+        # nrm_tune: the same autotuner without the read-back
+        import ctypes
+        L = nrm.load()
+        lens = np.ascontiguousarray(np.diff(off), dtype=np.int64)
+        assert L.nrm_tune(ctx.h, code, ctypes.c_void_p(lens.ctypes.data), lens.size) == 0
+        assert L.nrm_tune(ctx.h, code, None, 4) == nrm.NRM_EINVAL
+        out, _ = nrm.nrm_batch(dev(xb), dev(off), ctx=ctx)
+        assert bits_equal(out.cpu().numpy(), oracle.nrm_batch(xb, off))
     finally:
         ctx.close()
 
