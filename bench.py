@@ -58,10 +58,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # summaries are committed beside the code); set the flag to False whenever
 # the binary64 tree kernel changes, and re-capture.
 NCU_VALID = True
-TRAFFIC_D_2E28 = 2186.772736e6 + 106.839296e6  # DNRMF: DRAM read + write of one launch at n = 2^28
-TRAFFIC_S_2E28 = 1076.780288e6 + 39.507456e6  # SNRMF: the same
-INST_PER_ELEM_D = 166.6  # DNRMF: smsp__inst_executed.sum x 32 / n at n = 2^26 (thread-instructions per element)
-ALU_PER_ELEM_D = 88.87   # DNRMF: sm__inst_executed_pipe_alu.sum x 32 / n at n = 2^26 (the ALU pipe: 64 lanes an SM)
+TRAFFIC_D_2E28 = 2184.543488e6 + 111.279616e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1076.674560e6 + 39.069184e6  # SNRMF: the same
+INST_PER_ELEM_D = 144.4  # DNRMF: smsp__inst_executed.sum x 32 / n at n = 2^26 (thread-instructions per element)
+ALU_PER_ELEM_D = 73.62   # DNRMF: sm__inst_executed_pipe_alu.sum x 32 / n at n = 2^26 (the ALU pipe: 64 lanes an SM)
 ALU_PER_SM_CLK = 64
 FP64_PER_COMBINE_D = 2   # DNRMF: one DFMA (S = 1 + Q^2) and one DMUL (h = M s) per v1_hypot
 ISSUE_PER_SM_CLK = 4 * 32  # thread-instructions an SM issues per clock (4 schedulers x 1 warp-instruction)

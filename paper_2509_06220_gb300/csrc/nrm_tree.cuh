@@ -409,10 +409,11 @@ __device__ __forceinline__ void store_plan(VecPlan *dst, const VecPlan &pl) {
     for (int w = 0; w < 6; ++w) __stcg(d + w, src[w]);
 }
 
-// One block of 1024 threads.  Thread t handles vectors t, t + 1024, ...
-// (rounds), so that the offset loads and the status and output stores of a
-// warp are coalesced; prefix sums over the vectors run round by round with
-// the running totals carried along.
+// One block of 1024 threads.  Thread t handles the vectors of one
+// contiguous chunk, [t c, (t + 1) c) with c = ceil(B / 1024), so that each
+// prefix sum (ticket nodes in vector order, item bases in plan order) is a
+// single block scan of the threads' chunk totals; a chunk is read two
+// vectors at a time, their offset loads issued together.
 template <typename T>
 __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ off, const int64_t *__restrict__ lens,
                                                     const double *__restrict__ pdev, int64_t B, int64_t x_len,
@@ -421,18 +422,36 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
                                                     unsigned long long *cursor,
                                                     T *out, int32_t *status) {
     constexpr int P = Geo<T>::P;
+    constexpr int U = 2; // vectors whose loads are issued together
     __shared__ int64_t s_warp[32];
     const int tid = threadIdx.x;
-    const int64_t rounds = (B + 1023) / 1024;
+    const int64_t C = (B + 1023) / 1024;
+    const int64_t v0 = min((int64_t)tid * C, B), v1 = min(v0 + C, B);
     int kk = kitem; // work-item depth; deepened below if the tickets would not fit
-    auto plan_of = [&](int64_t v, VecPlan &pl, int64_t &items, int64_t &nodes, int32_t &st) {
-        const int64_t a = off[v];
-        const int64_t b = lens ? ((lens[v] >= 0 && a <= x_len - lens[v]) ? a + lens[v] : -1) : off[v + 1];
+    // a vector's segment [a, b) (b = -1 for a bad length) and p
+    struct Seg {
+        int64_t a, b;
+        double p;
+    };
+    auto load_seg = [&](int64_t v) {
+        Seg g;
+        g.a = off[v];
+        if (lens) {
+            const int64_t l = lens[v];
+            g.b = (l >= 0 && g.a <= x_len - l) ? g.a + l : -1;
+        } else {
+            g.b = off[v + 1];
+        }
+        g.p = pdev ? pdev[v] : 2.0;
+        return g;
+    };
+    auto plan_of = [&](const Seg &g, VecPlan &pl, int64_t &items, int64_t &nodes, int32_t &st) {
+        const int64_t a = g.a, b = g.b;
         pl = VecPlan{};
         items = 0;
         nodes = 0;
         st = NRM_OK;
-        if (a < 0 || b < a || b > x_len || (pdev && !plan_op<T>(pdev[v], pl))) {
+        if (a < 0 || b < a || b > x_len || (pdev && !plan_op<T>(g.p, pl))) {
             st = NRM_EINVAL;
             return;
         }
@@ -489,29 +508,36 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     // Segments may overlap, so their nodes are not bounded by x_len: if the
     // nodes exceed the workspace, deeper work items need fewer of them (the
     // tree is unchanged), and the pass is repeated at the next depth.
-    int64_t total_nodes;
+    int64_t total_nodes, node_excl;
     for (;;) {
         for (int q = tid; q < NB; q += 1024) s_cnt[q] = s_cur[q] = 0u;
         __syncthreads();
         int64_t tn = 0;
-        for (int64_t r = 0; r < rounds; ++r) {
-            const int64_t v = r * 1024 + tid;
-            const bool valid = v < B;
-            int64_t it = 0, nd = 0;
-            int q = NB; // no class
-            if (valid) {
-                VecPlan pl;
-                int32_t st;
-                plan_of(v, pl, it, nd, st);
-                q = bucket_of(pl, it);
+        for (int64_t j0 = 0; j0 < C; j0 += U) {
+            Seg g[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (v0 + j0 + u < v1) g[u] = load_seg(v0 + j0 + u);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool valid = v0 + j0 + u < v1;
+                int64_t it = 0, nd = 0;
+                int q = NB; // no class
+                if (valid) {
+                    VecPlan pl;
+                    int32_t st;
+                    plan_of(g[u], pl, it, nd, st);
+                    q = bucket_of(pl, it);
+                }
+                const unsigned grp = __match_any_sync(FULL, q);
+                if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
+                tn += nd;
             }
-            const unsigned grp = __match_any_sync(FULL, q);
-            if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
-            int64_t sn;
-            block_scan_1024(nd, s_warp, &sn);
-            tn += sn;
         }
-        total_nodes = tn;
+        int64_t sn;
+        const int64_t incl = block_scan_1024(tn, s_warp, &sn);
+        node_excl = incl - tn;
+        total_nodes = sn;
         if (total_nodes <= node_cap || kk >= kmax) break;
         ++kk;
     }
@@ -532,57 +558,61 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     }
     // the plans, in class order, with their item counts in item_base for
     // now; statuses and the outputs of empty or bad vectors
-    int64_t nbase = 0; // ticket nodes of the earlier rounds
-    for (int64_t r = 0; r < rounds; ++r) {
-        const int64_t v = r * 1024 + tid;
-        const bool valid = v < B;
-        VecPlan pl;
-        int64_t it = 0, nd = 0;
-        int q = NB;
-        if (valid) {
-            int32_t st;
-            plan_of(v, pl, it, nd, st);
-            if (overflow) {
-                it = 0;
-                if (st == NRM_OK) st = NRM_ENOMEM;
+    int64_t nbase = node_excl; // ticket nodes of the vectors before this one
+    for (int64_t j0 = 0; j0 < C; j0 += U) {
+        Seg g[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (v0 + j0 + u < v1) g[u] = load_seg(v0 + j0 + u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t v = v0 + j0 + u;
+            const bool valid = v < v1;
+            VecPlan pl;
+            int64_t it = 0, nd = 0;
+            int q = NB;
+            if (valid) {
+                int32_t st;
+                plan_of(g[u], pl, it, nd, st);
+                if (overflow) {
+                    it = 0;
+                    if (st == NRM_OK) st = NRM_ENOMEM;
+                }
+                if (status) status[v] = st;
+                if (st != NRM_OK) out[v] = T(NAN);
+                else if (pl.n == 0) out[v] = T(0);
+                q = bucket_of(pl, it);
             }
-            if (status) status[v] = st;
-            if (st != NRM_OK) out[v] = T(NAN);
-            else if (pl.n == 0) out[v] = T(0);
-            q = bucket_of(pl, it);
+            const unsigned grp = __match_any_sync(FULL, q);
+            const int leader = __ffs(grp) - 1;
+            unsigned base = 0u;
+            if (valid && lane == leader) base = atomicAdd(&s_cur[q], (unsigned)__popc(grp));
+            base = __shfl_sync(FULL, base, leader);
+            if (valid) {
+                pl.node_base = nbase;
+                pl.out_idx = v;
+                pl.item_base = it;
+                const int64_t slot = s_vbase[q] + base + __popc(grp & lt);
+                store_plan(plans + slot, pl);
+                if (slot < PLAN_SMEM) s_items[slot] = (int32_t)it;
+            }
+            nbase += nd;
         }
-        int64_t sn;
-        const int64_t incl = block_scan_1024(nd, s_warp, &sn);
-        const unsigned grp = __match_any_sync(FULL, q);
-        const int leader = __ffs(grp) - 1;
-        unsigned base = 0u;
-        if (valid && lane == leader) base = atomicAdd(&s_cur[q], (unsigned)__popc(grp));
-        base = __shfl_sync(FULL, base, leader);
-        if (valid) {
-            pl.node_base = nbase + incl - nd;
-            pl.out_idx = v;
-            pl.item_base = it;
-            const int64_t slot = s_vbase[q] + base + __popc(grp & lt);
-            store_plan(plans + slot, pl);
-            if (slot < PLAN_SMEM) s_items[slot] = (int32_t)it;
-        }
-        nbase += sn;
     }
     __syncthreads(); // the plans are written (visible within the block)
-    // item bases in plan order, round by round
-    int64_t ibase = 0;
-    for (int64_t r = 0; r < rounds; ++r) {
-        const int64_t s = r * 1024 + tid;
-        const int64_t c = s < B ? (s < PLAN_SMEM ? (int64_t)s_items[s] : plans[s].item_base) : 0;
-        int64_t tot;
-        const int64_t incl = block_scan_1024(c, s_warp, &tot);
-        if (s < B) {
-            plans[s].item_base = ibase + incl - c;
-            bases[s] = ibase + incl - c;
-        }
-        ibase += tot;
+    // item bases in plan order: thread t takes the plan slots [t c, (t + 1) c)
+    auto items_at = [&](int64_t sl) { return sl < PLAN_SMEM ? (int64_t)s_items[sl] : plans[sl].item_base; };
+    int64_t ci = 0;
+    for (int64_t sl = v0; sl < v1; ++sl) ci += items_at(sl);
+    int64_t total_items;
+    const int64_t iincl = block_scan_1024(ci, s_warp, &total_items);
+    int64_t run = iincl - ci;
+    for (int64_t sl = v0; sl < v1; ++sl) {
+        const int64_t c = items_at(sl);
+        plans[sl].item_base = run;
+        bases[sl] = run;
+        run += c;
     }
-    const int64_t total_items = ibase;
     if (tid == 0) {
         totals[0] = overflow ? 0 : total_items;
         totals[1] = total_nodes;

@@ -14,7 +14,11 @@ bounds hold for any approximation at least that good.  Checked:
   (floor(Num 2^53 / B) + 1) / 2 is RN(Num 2^52 / B) (no ties in division);
 - the integer square root of (2^52 + F) 2^(52 + o): the candidate TT is the
   floor or one above it, the intermediate remainders stay below 2^36 and
-  2^43, and TT - 1 + [W3 > -TT] + [W3 > TT] is RN(sqrt(N)).
+  2^43, and TT - 1 + [W3 > -TT] + [W3 > TT] is RN(sqrt(N));
+- the paired form's square root (o = 0): the last digit taken for
+  2 sqrt(N) (the same estimate times 2), TT2 = 2 Tp + T3 the floor of
+  2 sqrt(N) or one above it, W3 = 4 N - TT2^2, and
+  (TT2 - [W3 < 0] + 1) / 2 is RN(sqrt(N)).
 """
 import math
 import random
@@ -136,6 +140,43 @@ def isqrt_rn(f, o, ap, stats):
     return tt - 1 + (1 if w3 > -tt else 0) + (1 if w3 > tt else 0)
 
 
+def isqrt_rn2(sint, ap, stats):
+    """RN(sqrt(N)) for N = sint 2^52, sint = 2^52 + f in [2^52, 2^53]: the
+    paired kernels' form (the FP32 value of sint 2^-52 from sint's bits, the
+    first remainder from (T1 2^6)^2, the last digit for 2 sqrt(N))."""
+    fs = bitsf(0x3F000000 + ((sint >> 29) & 0xFFFFFFFF))
+    assert fs == (bitsf(0x3F800000 | ((sint - HID) >> 29)) if sint < 2 * HID else f32(2.0))
+    y0 = ap.rsqrt(fs)
+    e = fma32(-mul32(fs, y0), y0, f32(1))
+    y = fma32(mul32(y0, f32(0.5)), e, y0)
+    t1 = round_small(mul32(mul32(fs, y), f32(2.0 ** 20)))
+    assert 0 <= t1 << 6 < 2 ** 32
+    w1 = s64(sint - (t1 << 6) * (t1 << 6))
+    assert w1 == s64(sint - ((t1 * t1) << 12)) and abs(w1) < 2 ** 36
+    t2 = round_small(mul32(mul32(i2f(w1 >> 8), y), f32(2.0 ** -5)))
+    # the cross term as one signed 32 x 32 product: t1 2^10 and t2 2^11 fit
+    assert 0 <= t1 * 1024 < 2 ** 31 and -2 ** 31 <= t2 * 2048 < 2 ** 31
+    w2 = s64((w1 << 28) - (t1 * 1024) * (t2 * 2048) - t2 * t2)
+    assert w2 == s64((w1 << 28) - ((2 * t1 * t2) << 20) - t2 * t2)
+    assert abs(w2) < 2 ** 43
+    stats["t2"] = max(stats.get("t2", 0), abs(t2))
+    t3 = round_small(mul32(mul32(i2f(w2 >> 16), y), f32(2.0 ** -12)))
+    tp2 = (t1 << 33) + (t2 << 13)
+    w3 = s64((w2 << 26) - s64(tp2 * 2 * t3) - t3 * t3)
+    n = sint << 52
+    tt2 = tp2 + t3
+    assert w3 == 4 * n - tt2 * tt2
+    fl2 = math.isqrt(4 * n)
+    stats["sqrt2"].add(tt2 - fl2)
+    assert tt2 - fl2 in (0, 1), "candidate is not the floor of 2 sqrt(N) or one above it"
+    u = tp2 + (t3 + 1 + (-1 if w3 < 0 else 0))
+    assert u - 1 == fl2
+    # the bits of s = RN(sqrt(N)) 2^-52 with 1/2's added doubled before the halving
+    sbits = (tp2 + (0x3FE0000000000000 << 1) + (t3 + 1 + (-1 if w3 < 0 else 0))) >> 1
+    assert sbits == 0x3FF0000000000000 | ((u >> 1) & (HID - 1))
+    return (u & M64) >> 1
+
+
 def rn_quotient(num, b):
     fl, rem = divmod(num << 52, b)
     return fl + (1 if 2 * rem > b or (2 * rem == b and fl & 1) else 0)
@@ -187,6 +228,29 @@ def test_rounded_square_root_digits():
     assert stats["sqrt"] <= {0, 1}
 
 
+def test_rounded_square_root_paired_form():
+    rng = random.Random(31)
+    ap = Approx(random.Random(32))
+    stats = {"sqrt2": set()}
+    fs = [0, 1, 2, HID - 1, HID - 2, HID, 1 << 51, (1 << 51) + 1]
+    for _ in range(2000):
+        fs.append(rng.getrandbits(52))
+        t = (1 << 52) + rng.getrandbits(52)
+        f2 = ((t * t + t) >> 52) - HID   # roots next to a half-integer
+        if 0 <= f2 < HID:
+            fs.append(f2)
+        f3 = ((t * t) >> 52) - HID       # roots next to an integer
+        if 0 <= f3 < HID:
+            fs.append(f3)
+    for f in fs:
+        n = (HID + f) << 52
+        assert isqrt_rn2(HID + f, ap, stats) == rn_sqrt(n), f
+    assert stats["sqrt2"] == {0, 1}
+    # |T2| <= 2^20 |2^20 sqrt(S 2^-52) - T1| + small, and T1 is within
+    # 1/2 + 0.18 (the estimate) + 0.09 (the truncated fS) of 2^20 sqrt(S 2^-52)
+    assert stats["t2"] < 0.8 * 2 ** 20
+
+
 def test_division_has_no_ties():
     """The fact that lets the kernels round the quotient from one extra bit:
     2 Num 2^52 / B is never an odd integer for 53-bit significands (it would
@@ -205,3 +269,15 @@ def test_division_has_no_ties():
         num = b + rng.randrange(b)
         q2, r = divmod(num << 53, b)
         assert not (r == 0 and q2 & 1)
+
+
+def test_dividend_shifts_of_the_paired_form():
+    """The paired form takes Num 2^20 (mod 2^64) and floor(Num 2^-29) as single
+    shifts of A (Num = A or 2A): A << s and A >> (49 - s), s = 20 or 21."""
+    rng = random.Random(41)
+    for _ in range(5000):
+        a, b = HID | rng.getrandbits(52), HID | rng.getrandbits(52)
+        num = a if a >= b else a << 1
+        s = 20 if a >= b else 21
+        assert (a << s) & M64 == (num << 20) & M64
+        assert a >> (49 - s) == num >> 29
