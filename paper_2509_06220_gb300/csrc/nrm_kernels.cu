@@ -95,8 +95,11 @@ extern "C" nrm_status nrm_create(nrm_ctx **ctx, int device) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, device);
     c->sms = prop.multiProcessorCount;
-    // defaults from a sweep on GB300 at n = 2^28 with the item cursor (the
-    // autotuner refines them): items of 2^7 rows, 4 warps a block
+    // defaults from sweeps on GB300 at n = 2^28 with the item cursor (the
+    // autotuner refines them per shape): items of 2^7 rows, 4 warps a block
+    // (for one binary64 vector of 2^28, items of 2^8 rows are 3 % faster at
+    // the 80-register cap, but they halve the items of a batch of shorter
+    // vectors)
     c->tune[NRM_F32] = nrm_tuning{2, 4, 7, 16};
     c->tune[NRM_F64] = nrm_tuning{2, 4, 7, 8};
     nrm_status s = nrm_ctx_ensure(c, (size_t)4 << 20, 1 << 16);

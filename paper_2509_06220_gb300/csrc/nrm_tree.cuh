@@ -300,11 +300,12 @@ __global__ void __maxnreg__(Op::kMaxRegs) tree_kernel(TreeArgs<T> a, Op op) {
 // A ragged batch with a p per vector: the same persistent loop, each work
 // item combined with its vector's op (a warp-uniform switch: an item belongs
 // to one vector), so every result is bitwise that of the single-p kernel for
-// that vector's p.  Register cap: binary64 64, the cap of all its ops;
-// binary32 takes v1_lp's (at v1_hypot's 72 the binary32 v1_lp spills:
-// 2.33 ms against 1.46 ms).
+// that vector's p.  Register cap: v1_lp's in both precisions (binary64 64:
+// its pows are out-of-line calls, and 64 registers keep twice the warps of
+// 128 resident; at binary32 v1_hypot's 72 the binary32 v1_lp spills: 2.33
+// ms against 1.46 ms).
 template <typename T> struct MixedRegs {
-    static constexpr int value = sizeof(T) == 8 ? OpHypot<T>::kMaxRegs : OpLp<T>::kMaxRegs;
+    static constexpr int value = OpLp<T>::kMaxRegs;
 };
 template <typename T, int G>
 __global__ void __maxnreg__(MixedRegs<T>::value) tree_kernel_mixed(TreeArgs<T> a) {
