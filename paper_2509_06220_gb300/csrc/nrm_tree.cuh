@@ -484,9 +484,9 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
     // with their output index, and their item bases increasing with the
     // plan index.  With a p per vector the classes are ordered by combine
     // first (v1_lp, v1_hypot, maxabs, sumabs: the costliest first).  Within
-    // a class the order comes from warp-aggregated shared-memory atomics, so
-    // it may differ between calls: it decides which warp computes a subtree,
-    // never the tree.  Ticket nodes keep the vector order.
+    // a class the order comes from shared-memory atomics, so it may differ
+    // between calls: it decides which warp computes a subtree, never the
+    // tree.  Ticket nodes keep the vector order.
     constexpr int NL = 4 * 41 + 1;   // length classes
     constexpr int NB = 4 * NL;       // (combine, length) classes, NB <= 1024
     __shared__ unsigned s_cnt[NB], s_cur[NB];
@@ -503,8 +503,6 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
         const int rank = !pdev ? 0 : pl.op == OP_LP ? 0 : pl.op == OP_HYPOT ? 1 : pl.op == OP_MAXABS ? 2 : 3;
         return rank * NL + (NL - 2 - cls);
     };
-    const int lane = tid & 31;
-    const unsigned lt = (1u << lane) - 1u; // lanes below this one
     // One pass: the ticket nodes of all vectors and the class counts.
     // Segments may overlap, so their nodes are not bounded by x_len: if the
     // nodes exceed the workspace, deeper work items need fewer of them (the
@@ -530,8 +528,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
                     plan_of(g[u], pl, it, nd, st);
                     q = bucket_of(pl, it);
                 }
-                const unsigned grp = __match_any_sync(FULL, q);
-                if (valid && (grp & lt) == 0u) atomicAdd(&s_cnt[q], (unsigned)__popc(grp));
+                if (valid) atomicAdd(&s_cnt[q], 1u);
                 tn += nd;
             }
         }
@@ -584,16 +581,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(const int64_t *__restrict__ 
                 else if (pl.n == 0) out[v] = T(0);
                 q = bucket_of(pl, it);
             }
-            const unsigned grp = __match_any_sync(FULL, q);
-            const int leader = __ffs(grp) - 1;
-            unsigned base = 0u;
-            if (valid && lane == leader) base = atomicAdd(&s_cur[q], (unsigned)__popc(grp));
-            base = __shfl_sync(FULL, base, leader);
             if (valid) {
                 pl.node_base = nbase;
                 pl.out_idx = v;
                 pl.item_base = it;
-                const int64_t slot = s_vbase[q] + base + __popc(grp & lt);
+                const int64_t slot = s_vbase[q] + atomicAdd(&s_cur[q], 1u);
                 store_plan(plans + slot, pl);
                 if (slot < PLAN_SMEM) s_items[slot] = (int32_t)it;
             }
