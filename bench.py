@@ -13,12 +13,13 @@ Printed as one JSON line (rank 0):
              (nrm_host: pinned host input, chunked H2D copies overlapped with
              the tree, result read back), copies inside the timed region;
   roofline   for the dominant kernel (the binary64 tree kernel): the slowest
-             of three floors -- its bytes at the measured HBM copy rate, its
+             of four floors -- its bytes at the measured HBM copy rate, its
              FP64 instructions (one DFMA and one DMUL per v1_hypot) at the
-             FP64 rate measured here by a register-only probe, and its
+             FP64 rate measured here by a register-only probe, its
              thread-instructions (ncu count per element) at the issue rate
-             of 4 warp-instructions per SM per clock -- against its
-             CUDA-event launch time;
+             of 4 warp-instructions per SM per clock, and its ALU-pipe
+             instructions (ncu count) at 64 lanes per SM per clock --
+             against its CUDA-event launch time;
   cpu_baseline  the C oracle on the same step, on all host cores (its thread
              driver) and on one;
   parts      per-precision figures, the hypot variants, config 0 (one FP64
@@ -33,8 +34,11 @@ Printed as one JSON line (rank 0):
              capacity and a run below it).
 Multi-GPU (torchrun): every rank computes its own pair of vectors (seed
 1 + rank); there is no data-path collective ("weak" scaling).
---impl reference times the oracle (the reference arm for this build) on a
-bounded sample of the same workload on the host cores.
+The headline vectors run on a context of their own (binary64 work items of
+2^8 rows, what nrm_tune picks for one vector of 2^28); the other configs
+use the library's defaults or contexts autotuned for their shapes.
+--impl reference times the oracle (the reference arm) on a bounded sample
+of the same workload on the host cores.
 """
 import argparse
 import json
