@@ -34,8 +34,8 @@ Printed as one JSON line (rank 0):
              capacity and a run below it).
 Multi-GPU (torchrun): every rank computes its own pair of vectors (seed
 1 + rank); there is no data-path collective ("weak" scaling).
-The headline vectors run on a context of their own (binary64 work items of
-2^8 rows, what nrm_tune picks for one vector of 2^28); the other configs
+The headline vectors run on a context of their own (work items of 2^8 rows,
+what nrm_tune picks for one vector of 2^28 in either precision); the other configs
 use the library's defaults or contexts autotuned for their shapes.
 --impl reference times the oracle (the reference arm) on a bounded sample
 of the same workload on the host cores.
@@ -62,8 +62,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # summaries are committed beside the code); set the flag to False whenever
 # the binary64 tree kernel changes, and re-capture.
 NCU_VALID = True
-TRAFFIC_D_2E28 = 2149.692416e6 + 45.529088e6  # DNRMF: DRAM read + write of one launch at n = 2^28
-TRAFFIC_S_2E28 = 1078.284288e6 + 39.130368e6  # SNRMF: the same
+TRAFFIC_D_2E28 = 2149.612544e6 + 45.566976e6  # DNRMF: DRAM read + write of one launch at n = 2^28
+TRAFFIC_S_2E28 = 1079.169280e6 + 18.969856e6  # SNRMF: the same
 INST_PER_ELEM_D = 141.3  # DNRMF: smsp__inst_executed.sum x 32 / n at n = 2^26 (thread-instructions per element)
 ALU_PER_ELEM_D = 72.86   # DNRMF: sm__inst_executed_pipe_alu.sum x 32 / n at n = 2^26 (the ALU pipe: 64 lanes an SM)
 ALU_PER_SM_CLK = 64
@@ -575,14 +575,15 @@ def main():
         torch.cuda.synchronize()
 
     ctx = nrm.context(local)
-    # The headline vectors run on a context of their own: binary64 work items
-    # of 2^8 rows, up to 8 blocks of 4 warps an SM (the 80-register cap of
-    # the binary64 v1_hypot lets 6 reside), the setting a sweep at n = 2^28
+    # The headline vectors run on a context of their own: work items of 2^8
+    # rows, 4 warps a block, up to 8 (binary64; its 80-register cap lets 6
+    # reside) or 16 (binary32) blocks an SM, the settings sweeps at n = 2^28
     # and nrm_tune for one vector of 2^28 pick; the library defaults (items of
     # 2^7 rows, better for batches of shorter vectors) stay on `ctx` for
     # configs 0, 2 and 3.
     hctx = nrm.Context(local)
     hctx.set_tuning(group_log2=2, warps_per_block=4, item_log2=8, blocks_per_sm=8, dtype=nrm.NRM_F64)
+    hctx.set_tuning(group_log2=2, warps_per_block=4, item_log2=8, blocks_per_sm=16, dtype=nrm.NRM_F32)
     # the FP64 pipe's measured rate (register-only DFMA chains), before the
     # timed region
     fp64_rate = nrm.probe_pipe(nrm.PIPE_DFMA, iters=4096, blocks_per_sm=8)
