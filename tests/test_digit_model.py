@@ -18,7 +18,10 @@ bounds hold for any approximation at least that good.  Checked:
 - the paired form's square root (o = 0): the last digit taken for
   2 sqrt(N) (the same estimate times 2), TT2 = 2 Tp + T3 the floor of
   2 sqrt(N) or one above it, W3 = 4 N - TT2^2, and
-  (TT2 - [W3 < 0] + 1) / 2 is RN(sqrt(N)).
+  (TT2 - [W3 < 0] + 1) / 2 is RN(sqrt(N));
+- two identities of the restricted pow's integer steps: the final
+  round-to-nearest-even as one carry, and 128-bit negation as
+  (v ^ mask) - mask.
 """
 import math
 import random
@@ -281,3 +284,58 @@ def test_dividend_shifts_of_the_paired_form():
         s = 20 if a >= b else 21
         assert (a << s) & M64 == (num << 20) & M64
         assert a >> (49 - s) == num >> 29
+
+
+def test_pow_final_rounding_by_carry():
+    """The restricted pow's last step rounds P in [2^126, 2^128) (two 64-bit
+    words) to 53 bits, ties to even, as one carry: q = hi >> sh, the bits
+    below q (hi mod 2^sh, with lo != 0 OR-ed into bit 0 as a sticky bit,
+    which lies below the half bit since sh >= 10) plus half - 1 plus q's
+    last bit carry into bit sh exactly when q rounds up."""
+    rng = random.Random(51)
+    cases = []
+    for _ in range(20000):
+        top = rng.randrange(2)
+        hi = (1 << (62 + top)) | rng.getrandbits(62 + top)
+        lo = rng.getrandbits(64) if rng.random() < 0.7 else 0
+        sh = 10 + top
+        # push some cases to exact halves and to the neighbours of halves
+        if rng.random() < 0.3:
+            hi = (hi >> sh << sh) | (1 << (sh - 1)) | rng.choice([0, 0, 1])
+            if rng.random() < 0.5:
+                lo = 0
+        cases.append((hi, lo))
+    cases.append(((1 << 64) - 1, (1 << 64) - 1))  # rounds up to 2^53
+    for hi, lo in cases:
+        top = hi >> 63
+        sh = 10 + top
+        q = hi >> sh
+        half = 1 << (sh - 1)
+        low = (hi & (2 * half - 1)) | (1 if lo else 0)
+        m = q + ((low + (half - 1) + (q & 1)) >> sh)
+        # reference: round half to even of (hi 2^64 + lo) / 2^(64 + sh)
+        num, den = (hi << 64) | lo, 1 << (64 + sh)
+        fl, rem = divmod(num, den)
+        ref = fl + (1 if 2 * rem > den or (2 * rem == den and fl & 1) else 0)
+        assert m == ref, (hex(hi), hex(lo))
+
+
+def test_masked_negation_of_128_bit_values():
+    """(v ^ mask) - mask is v for mask = 0 and -v (mod 2^128) for mask = all
+    ones, the form the restricted pow uses to take |W| and to give the sign
+    back, applied to the two 64-bit words with a borrow between them."""
+    rng = random.Random(52)
+    M128 = (1 << 128) - 1
+    for _ in range(5000):
+        v = rng.getrandbits(128)
+        for neg in (False, True):
+            mk = M128 if neg else 0
+            got = ((v ^ mk) - mk) & M128
+            assert got == ((-v) & M128 if neg else v)
+            # word by word: the low word's borrow enters the high word
+            m64 = (1 << 64) - 1 if neg else 0
+            vh, vl = v >> 64, v & ((1 << 64) - 1)
+            lo = (vl ^ m64) - m64
+            borrow = 1 if lo < 0 else 0
+            hi = ((vh ^ m64) - m64 - borrow) & ((1 << 64) - 1)
+            assert (hi << 64) | (lo & ((1 << 64) - 1)) == got
